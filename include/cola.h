@@ -1,0 +1,138 @@
+/*
+ * cola.h — C ABI of the GB300 (sm_103a) COLA particle-mesh library.
+ *
+ * The method is COLA (COmoving Lagrangian Acceleration) as used by Koda et al. 2015,
+ * "Fast and accurate mock catalogue generation for low-mass galaxies" (arXiv:1507.05329):
+ * particles move relative to their 2LPT trajectories (§2.1), the residual is integrated with the
+ * kick and drift of §2.2 eqs. (cola-kick) and (cola-drift) on the time grid a_i = i/n_step
+ * (eq. drift-a), and the force is a particle-mesh (PM) force on a uniform mesh (§2.3).
+ *
+ * Conventions used by every call
+ *   - Units: H0 = 1; lengths in PM mesh cells (L/N); time variable a; canonical velocity
+ *     v = a^2 dx/dt (§2.2, eq. motion).
+ *   - Particles: n = np^3, particle id = (ix*np + iy)*np + iz on the Lagrangian lattice q.
+ *     Every particle array is structure-of-arrays float32 [3][n] (x block, then y, then z),
+ *     a DEVICE pointer owned by the caller, 16-byte aligned.
+ *       s    : total displacement x - q (mesh cells);
+ *       v    : residual canonical velocity v_res = v - a^2 dx_2LPT/dt (§2.1);
+ *       psi1 : first-order 2LPT displacement Psi1 (mesh cells);
+ *       psi2 : second-order 2LPT displacement Psi2 (mesh cells), x_2LPT = q + D1 Psi1 + D2 Psi2.
+ *   - Mesh arrays are [N][N][N] C order (z fastest).  Half spectra are [N][N][N/2+1] complex
+ *     (interleaved float re, im), the k_z >= 0 half as in §3.3.
+ *   - Calls are asynchronous on the context's CUDA stream unless stated; the caller must keep
+ *     buffers alive until the stream has finished with them.
+ *   - Errors: every int-returning call returns a cola_status.  Argument errors are found on the
+ *     host before anything is launched.  Device-side conditions (fixed-point overflow,
+ *     non-finite particle state) set a sticky flag that cola_sync() reports.
+ *   - One context per device and stream; a context is not thread safe.  The library keeps no
+ *     global state besides the contexts.
+ */
+#ifndef COLA_H
+#define COLA_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    COLA_OK = 0,
+    COLA_ERR_INVALID = 1,     /* bad argument or size (reported on the host, nothing launched) */
+    COLA_ERR_OOM = 2,         /* device allocation failed */
+    COLA_ERR_CUDA = 3,        /* a CUDA runtime call failed */
+    COLA_ERR_OVERFLOW = 4,    /* a fixed-point mesh cell overflowed (more than 2^22 particles) */
+    COLA_ERR_NONFINITE = 5    /* a particle position or velocity became NaN or infinite */
+} cola_status;
+
+/* Parameters of one realisation (§1 cosmology, §2.2 time stepping, §2.3 box and mesh).
+ * Flat LCDM with Omega_Lambda = 1 - omega_m; linear P(k) = A k^n_s T_BBKS(k)^2 normalised to
+ * sigma8 at a = 1.  Requirements (checked by cola_create): np >= 2 and nmesh >= 4 even, both with
+ * no prime factor above 5, nmesh <= 4096, np <= 2048, (nmesh * 2^20) % np == 0, nstep >= 1. */
+typedef struct {
+    double omega_m;       /* matter density today */
+    double h;             /* H0 / (100 km/s/Mpc), enters only Gamma = omega_m h of BBKS */
+    double n_s;           /* spectral index */
+    double sigma8;        /* rms of the linear density in 8 Mpc/h spheres at a = 1 */
+    double box;           /* box side L in Mpc/h */
+    int np;               /* particles per side */
+    int nmesh;            /* PM mesh cells per side */
+    int nstep;            /* n_step of eq. (drift-a); a_i = i / nstep */
+    double nlpt;          /* n_LPT of eqs. (ansatz-drift), (ansatz-kick); the paper uses -2.5 */
+    int ic_mode;          /* 0: eq. (initial_time), v_res = 0 at a_{1/2};
+                             1: Appendix A eq. (initial_time_original), v_res = 0 at a_1 */
+    int drift_ansatz;     /* 0: eq. (ansatz-drift); 1: v_res constant during a drift (§2.1) */
+} cola_params;
+
+typedef struct cola_ctx cola_ctx;
+
+/* Create a context on the current CUDA device for the given stream (cudaStream_t, NULL =
+ * legacy default stream).  Validates the parameters, computes every FP64 time coefficient on
+ * the host and allocates the device meshes (about 20 N^3 bytes plus the P(k) and FFT tables).
+ * The context owns those allocations.  Returns COLA_ERR_INVALID or COLA_ERR_OOM on failure and
+ * leaves *out NULL. */
+int cola_create(const cola_params* params, void* stream, cola_ctx** out);
+
+/* Free a context and its device memory (synchronises its stream first).  NULL is a no-op. */
+void cola_destroy(cola_ctx* ctx);
+
+/* Wait for the context's stream, then report and clear the sticky device error flag. */
+int cola_sync(cola_ctx* ctx);
+
+/* Human-readable text of a cola_status (static storage). */
+const char* cola_strerror(int status);
+
+/* FP64 scalars of COLA step i (1 <= i <= nstep), host only, no context needed.
+ * out[0..11] = a_i, a_lo, a_hi, force_scale = (3/2) Om / a_i, c1, c2 (2LPT acceleration
+ * coefficients, F_2LPT = c1 Psi1 + c2 Psi2), kick factor of eq. (cola-kick) from a_lo to a_hi,
+ * drift factor of eq. (cola-drift) from a_i to a_{i+1}, dD1, dD2 (growth increments over the
+ * drift), D1(a_i), D2(a_i).  The last step has drift = dD1 = dD2 = 0.  i = 0 returns the
+ * initial-condition scalars: out[0] = a_1, out[10] = D1(a_1), out[11] = D2(a_1), and out[8],
+ * out[9] = a^2 dD1/dt, a^2 dD2/dt at a = 1 (the 2LPT velocity factors of the final output).
+ * Returns COLA_ERR_INVALID for a bad index or nout < 12. */
+int cola_step_scalars(const cola_params* params, int i, double* out, int nout);
+
+/* S0 — 2LPT initial conditions (§2.1 growing mode; §2.3 2LPTic-style Gaussian modes).
+ * white_noise: device float32 [n], unit Gaussian, one value per lattice site (input).
+ * Writes psi1, psi2, s = D1(a_1) Psi1 + D2(a_1) Psi2 and v = 0 (eq. initial_time). */
+int cola_ic_2lpt(cola_ctx* ctx, const float* white_noise, float* s, float* v,
+                 float* psi1, float* psi2);
+
+/* S1 alone — CIC deposit of the particles at displacement s into rho (device uint64 [N^3]),
+ * which is overwritten.  Fixed point: mesh coordinate G = (q*R + rint(s*2^20)) mod N*2^20,
+ * R = (N/np)*2^20; cell G>>20; 14-bit weights; every particle adds exactly 2^42 (§2.3, §3.3
+ * CIC; the fixed-point form is this library's, deterministic and exact). */
+int cola_deposit(cola_ctx* ctx, const float* s, unsigned long long* rho);
+
+/* S1+S2 — deposit, then the forward 3D FFT of the density contrast
+ * delta = rho N^3 / (n 2^42) - 1.  delta_k: device float32 [N][N][N/2+1][2] (unnormalised DFT,
+ * X(k) = sum_x delta(x) exp(-i k.x)). */
+int cola_density_spectrum(cola_ctx* ctx, const float* s, float* delta_k);
+
+/* S1-S3 (+ interpolation) — PM force at the particles (§2.2 Poisson equation and eq. motion):
+ * F = -grad phi with nabla^2 phi = (3/2) Om a^-1 delta, Green function -1/k^2, 4-point
+ * central-difference gradient kernel, CIC interpolation with the deposit's weights.
+ * force: device float32 [3][n] in mesh cells per unit time squared. */
+int cola_pm_force(cola_ctx* ctx, const float* s, double a, float* force);
+
+/* S1-S5 — COLA step i (1 <= i <= nstep): force at a_i, kick v_res from a_{i-1/2} to a_{i+1/2}
+ * (eq. cola-kick, F_res = F - F_2LPT), drift s from a_i to a_{i+1} (eq. cola-drift) adding the
+ * 2LPT growth increments.  The last step kicks to a_nstep and does not drift.  In place on s, v. */
+int cola_step(cola_ctx* ctx, int i, float* s, float* v, const float* psi1, const float* psi2);
+
+/* A whole realisation: cola_ic_2lpt, then steps 1..nstep, then (if pk != NULL) the power
+ * spectrum of the final positions into pk (device double [3][nbins]). */
+int cola_run(cola_ctx* ctx, const float* white_noise, float* s, float* v, float* psi1,
+             float* psi2, double* pk, int nbins);
+
+/* S6 — matter power spectrum of the particles at displacement s (§3.3): CIC deposit, FFT, the
+ * modes {kz>0} U {kz=0,ky>0} U {kz=0,ky=0,kx>0}, nbins log-spaced bins between 2 pi/L and
+ * pi N/L decided on the integer |m|^2, P = V |delta_k|^2 / N^6 averaged per bin.
+ * pk: device double [3][nbins] = mean |k| (h/Mpc), P (Mpc/h)^3, mode count.  1 <= nbins <= 128.
+ * The reduction order is fixed, so the result is bit-reproducible.  A call with a different nbins
+ * than the previous one synchronises the stream once to upload the new bin edges. */
+int cola_power_spectrum(cola_ctx* ctx, const float* s, double* pk, int nbins);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* COLA_H */

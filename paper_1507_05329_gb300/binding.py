@@ -1,0 +1,203 @@
+"""Thin ctypes binding of the COLA C ABI (include/cola.h).
+
+Argument marshalling only: every step of the method runs in the CUDA library.  Tensors are torch
+CUDA tensors; the library never sees torch types, only device pointers, sizes and the stream.
+There is no CPU fallback: if libcola.so is missing or cannot be loaded, every call raises.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libcola.so")
+
+STATUS = {0: "ok", 1: "invalid argument or size", 2: "device allocation failed", 3: "CUDA runtime error",
+          4: "fixed-point density overflow", 5: "non-finite particle position or velocity"}
+
+
+class ColaError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {STATUS.get(status, 'unknown status')} (cola status {status})")
+        self.status = status
+
+
+class CParams(ctypes.Structure):
+    _fields_ = [("omega_m", ctypes.c_double), ("h", ctypes.c_double), ("n_s", ctypes.c_double),
+                ("sigma8", ctypes.c_double), ("box", ctypes.c_double), ("np", ctypes.c_int),
+                ("nmesh", ctypes.c_int), ("nstep", ctypes.c_int), ("nlpt", ctypes.c_double),
+                ("ic_mode", ctypes.c_int), ("drift_ansatz", ctypes.c_int)]
+
+
+@dataclasses.dataclass(frozen=True)
+class Params:
+    """Parameters of one realisation; field meanings as in cola_params (include/cola.h)."""
+
+    omega_m: float = 0.27
+    h: float = 0.7
+    n_s: float = 0.96
+    sigma8: float = 0.8
+    box: float = 256.0
+    np_side: int = 32
+    nmesh: int = 64
+    nstep: int = 10
+    nlpt: float = -2.5
+    ic_mode: int = 0
+    drift_ansatz: int = 0
+
+    @property
+    def n(self) -> int:
+        return self.np_side ** 3
+
+    def to_c(self) -> CParams:
+        return CParams(self.omega_m, self.h, self.n_s, self.sigma8, self.box, self.np_side, self.nmesh,
+                       self.nstep, self.nlpt, self.ic_mode, self.drift_ansatz)
+
+
+_LIB = None
+
+_VP, _I, _D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+SIGNATURES = {
+    "cola_create": ([ctypes.POINTER(CParams), _VP, ctypes.POINTER(_VP)], _I),
+    "cola_destroy": ([_VP], None),
+    "cola_sync": ([_VP], _I),
+    "cola_strerror": ([_I], ctypes.c_char_p),
+    "cola_step_scalars": ([ctypes.POINTER(CParams), _I, ctypes.POINTER(_D), _I], _I),
+    "cola_ic_2lpt": ([_VP, _VP, _VP, _VP, _VP, _VP], _I),
+    "cola_deposit": ([_VP, _VP, _VP], _I),
+    "cola_density_spectrum": ([_VP, _VP, _VP], _I),
+    "cola_pm_force": ([_VP, _VP, _D, _VP], _I),
+    "cola_step": ([_VP, _I, _VP, _VP, _VP, _VP], _I),
+    "cola_run": ([_VP, _VP, _VP, _VP, _VP, _VP, _VP, _I], _I),
+    "cola_power_spectrum": ([_VP, _VP, _VP, _I], _I),
+}
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libcola.so (raises if it is missing: there is no fallback path)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_1507_05329_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    for name, (args, res) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _LIB = lib
+    return lib
+
+
+def _check(status: int, what: str):
+    if status != 0:
+        raise ColaError(status, what)
+
+
+def step_scalars(p: Params, i: int) -> list[float]:
+    """The 12 FP64 scalars of step i (i = 0: initial-condition scalars), see cola_step_scalars."""
+    lib = load_library()
+    out = (ctypes.c_double * 12)()
+    cp = p.to_c()
+    _check(lib.cola_step_scalars(ctypes.byref(cp), i, out, 12), "cola_step_scalars")
+    return list(out)
+
+
+def _ptr(t, torch, shape=None, dtype=None):
+    if not t.is_cuda:
+        raise ValueError("COLA tensors must live on a CUDA device")
+    if not t.is_contiguous():
+        raise ValueError("COLA tensors must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"expected dtype {dtype}, got {t.dtype}")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"expected shape {tuple(shape)}, got {tuple(t.shape)}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Context:
+    """One realisation's device state (cola_ctx) bound to a CUDA stream."""
+
+    def __init__(self, params: Params, stream=None):
+        import torch
+        self.torch = torch
+        self.p = params
+        self.lib = load_library()
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self._ptr = ctypes.c_void_p()
+        cp = params.to_c()
+        _check(self.lib.cola_create(ctypes.byref(cp), ctypes.c_void_p(self.stream.cuda_stream),
+                                    ctypes.byref(self._ptr)), "cola_create")
+
+    # -- helpers ---------------------------------------------------------------------------
+    def _particles(self, t):
+        return _ptr(t, self.torch, (3, self.p.n), self.torch.float32)
+
+    def empty_particles(self):
+        return self.torch.empty((3, self.p.n), dtype=self.torch.float32, device=self.device)
+
+    @property
+    def device(self):
+        return self.stream.device
+
+    def close(self):
+        if self._ptr:
+            self.lib.cola_destroy(self._ptr)
+            self._ptr = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sync(self):
+        _check(self.lib.cola_sync(self._ptr), "cola_sync")
+
+    # -- calls -----------------------------------------------------------------------------
+    def ic_2lpt(self, white_noise):
+        wn = _ptr(white_noise, self.torch, (self.p.n,), self.torch.float32)
+        s, v, p1, p2 = (self.empty_particles() for _ in range(4))
+        _check(self.lib.cola_ic_2lpt(self._ptr, wn, self._particles(s), self._particles(v),
+                                     self._particles(p1), self._particles(p2)), "cola_ic_2lpt")
+        return s, v, p1, p2
+
+    def deposit(self, s):
+        n = self.p.nmesh
+        rho = self.torch.empty((n, n, n), dtype=self.torch.int64, device=self.device)
+        _check(self.lib.cola_deposit(self._ptr, self._particles(s), _ptr(rho, self.torch)), "cola_deposit")
+        return rho
+
+    def density_spectrum(self, s):
+        n = self.p.nmesh
+        dk = self.torch.empty((n, n, n // 2 + 1, 2), dtype=self.torch.float32, device=self.device)
+        _check(self.lib.cola_density_spectrum(self._ptr, self._particles(s), _ptr(dk, self.torch)),
+               "cola_density_spectrum")
+        return dk
+
+    def pm_force(self, s, a: float):
+        f = self.empty_particles()
+        _check(self.lib.cola_pm_force(self._ptr, self._particles(s), float(a), self._particles(f)),
+               "cola_pm_force")
+        return f
+
+    def step(self, i: int, s, v, psi1, psi2):
+        _check(self.lib.cola_step(self._ptr, int(i), self._particles(s), self._particles(v),
+                                  self._particles(psi1), self._particles(psi2)), "cola_step")
+
+    def power_spectrum(self, s, nbins: int = 64):
+        pk = self.torch.empty((3, nbins), dtype=self.torch.float64, device=self.device)
+        _check(self.lib.cola_power_spectrum(self._ptr, self._particles(s), _ptr(pk, self.torch), int(nbins)),
+               "cola_power_spectrum")
+        return pk
+
+    def run(self, white_noise, nbins: int = 64, with_pk: bool = True):
+        wn = _ptr(white_noise, self.torch, (self.p.n,), self.torch.float32)
+        s, v, p1, p2 = (self.empty_particles() for _ in range(4))
+        pk = self.torch.empty((3, nbins), dtype=self.torch.float64, device=self.device) if with_pk else None
+        _check(self.lib.cola_run(self._ptr, wn, self._particles(s), self._particles(v), self._particles(p1),
+                                 self._particles(p2), _ptr(pk, self.torch) if with_pk else None, int(nbins)),
+               "cola_run")
+        return dict(s=s, v=v, psi1=p1, psi2=p2, pk=pk)

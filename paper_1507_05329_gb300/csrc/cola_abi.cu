@@ -1,0 +1,378 @@
+// C ABI of the COLA particle-mesh library (declared in include/cola.h).
+//
+// One realisation per context.  The context owns the PM meshes and tables; the caller owns every
+// particle array.  Each call enqueues kernels on the context's stream:
+//   S0 cola_ic_2lpt ........ white noise -> delta_L -> Psi1, Psi2 (§2.1, §2.3)
+//   S1 deposit ............. CIC, 64-bit fixed point (§2.3, §3.3)
+//   S2 forward FFT ......... z (R2C, fused fixed-point -> delta), y
+//   S3 Poisson + gradient .. x forward fused with -1/k^2, the 4-point gradient and inverse x (x3);
+//                            then inverse y and C2R z for each component (§2.2 Poisson equation)
+//   S4+S5 gather/kick/drift  CIC interpolation + eqs. (cola-kick), (cola-drift) (§2.1, §2.2)
+//   S6 power spectrum ...... §3.3
+#include "cola_internal.h"
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+using namespace cola;
+
+namespace {
+
+#define COLA_TRY(expr)              \
+  do {                              \
+    const int _st = (expr);         \
+    if (_st != COLA_OK) return _st; \
+  } while (0)
+
+int cuda_status(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return COLA_OK;
+  std::fprintf(stderr, "cola: %s: %s\n", what, cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? COLA_ERR_OOM : COLA_ERR_CUDA;
+}
+
+bool smooth235(int n) {
+  if (n < 1) return false;
+  for (int p : {2, 3, 5})
+    while (n % p == 0) n /= p;
+  return n == 1;
+}
+
+int validate(const cola_params* p) {
+  if (!p) return COLA_ERR_INVALID;
+  if (p->np < 2 || p->np > 2048 || p->np % 2 || !smooth235(p->np)) return COLA_ERR_INVALID;
+  if (p->nmesh < 4 || p->nmesh > 4096 || p->nmesh % 2 || !smooth235(p->nmesh)) return COLA_ERR_INVALID;
+  if ((((long long)p->nmesh) << 20) % p->np) return COLA_ERR_INVALID;
+  if (p->nstep < 1 || p->nstep > 10000) return COLA_ERR_INVALID;
+  if (!(p->omega_m > 0.0 && p->omega_m <= 1.0) || !(p->box > 0.0) || !(p->h > 0.0) || !(p->sigma8 >= 0.0))
+    return COLA_ERR_INVALID;
+  if (!(p->nlpt != 0.0) || !std::isfinite(p->nlpt) || !std::isfinite(p->n_s)) return COLA_ERR_INVALID;
+  if (p->ic_mode < 0 || p->ic_mode > 1 || p->drift_ansatz < 0 || p->drift_ansatz > 1) return COLA_ERR_INVALID;
+  return COLA_OK;
+}
+
+Grid3 make_grid(int n) {
+  Grid3 g;
+  g.n = n;
+  g.nc = n / 2 + 1;
+  g.pc = (g.nc + 1) & ~1;   // even: complex rows start on 16-byte boundaries
+  return g;
+}
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+constexpr int kPkBlocks = 304;
+constexpr int kPkMaxBins = 128;
+
+// Integer |m|^2 lower edges of nbins log bins between |m| = 1 and |m| = N/2.
+void bin_edges(int nmesh, int nbins, long long* e) {
+  const double half = nmesh / 2.0;
+  for (int b = 0; b <= nbins; ++b) {
+    const double e2 = std::pow(half, 2.0 * b / nbins);
+    e[b] = (long long)std::ceil(e2 - 1e-9);
+  }
+}
+
+int check_ptr(const void* p) { return (p && ((uintptr_t)p % 16 == 0)) ? COLA_OK : COLA_ERR_INVALID; }
+
+// S1 + S2 (z, y): deposit and the first two forward passes into cbuf[2].
+int deposit_and_forward_yz(cola_ctx* c, const float* s) {
+  const Grid3& g = c->mesh;
+  const size_t n3 = (size_t)g.n * g.n * g.n;
+  COLA_TRY(cuda_status(cudaMemsetAsync(c->rho, 0, n3 * sizeof(unsigned long long), c->stream), "memset"));
+  COLA_TRY(launch_deposit(c->pg, s, c->rho, c->flags, c->stream));
+  const float scale = (float)((double)n3 / ((double)c->pg.npart * 4398046511104.0));   // N^3 / (n 2^42)
+  COLA_TRY(launch_r2c_rows(c->mplan, g, kSrcFixedPoint, c->rho, g.n, scale, c->cbuf[2], c->stream));
+  COLA_TRY(launch_pencils(c->mplan, g, 1, -1, c->cbuf[2], c->stream));
+  return COLA_OK;
+}
+
+// S1-S3: the three force components as real fields in cbuf[0..2] (rows of 2 pc floats).
+int force_mesh(cola_ctx* c, const float* s, double force_scale) {
+  const Grid3& g = c->mesh;
+  COLA_TRY(deposit_and_forward_yz(c, s));
+  float2* const outs[3] = {c->cbuf[0], c->cbuf[1], c->cbuf[2]};
+  COLA_TRY(launch_green_x(c->mplan, g, c->cbuf[2], outs, c->dtab, (float)force_scale, c->stream));
+  for (int j = 0; j < 3; ++j) {
+    COLA_TRY(launch_pencils(c->mplan, g, 1, +1, c->cbuf[j], c->stream));
+    COLA_TRY(launch_c2r_rows(c->mplan, g, c->cbuf[j], c->stream));
+  }
+  return COLA_OK;
+}
+
+int inverse3d(cola_ctx* c, const Grid3& g, const FftPlan& p, float2* b) {
+  COLA_TRY(launch_pencils(p, g, 0, +1, b, c->stream));
+  COLA_TRY(launch_pencils(p, g, 1, +1, b, c->stream));
+  return launch_c2r_rows(p, g, b, c->stream);
+}
+
+int forward3d_yx(cola_ctx* c, const Grid3& g, const FftPlan& p, float2* b) {
+  COLA_TRY(launch_pencils(p, g, 1, -1, b, c->stream));
+  return launch_pencils(p, g, 0, -1, b, c->stream);
+}
+
+}  // namespace
+
+extern "C" const char* cola_strerror(int status) {
+  switch (status) {
+    case COLA_OK: return "ok";
+    case COLA_ERR_INVALID: return "invalid argument or size";
+    case COLA_ERR_OOM: return "device allocation failed";
+    case COLA_ERR_CUDA: return "CUDA runtime error";
+    case COLA_ERR_OVERFLOW: return "fixed-point density overflow";
+    case COLA_ERR_NONFINITE: return "non-finite particle position or velocity";
+    default: return "unknown status";
+  }
+}
+
+extern "C" int cola_step_scalars(const cola_params* params, int i, double* out, int nout) {
+  if (validate(params) != COLA_OK || !out || nout < 12 || i < 0 || i > params->nstep) return COLA_ERR_INVALID;
+  const Cosmo cosmo(params->omega_m, params->h, params->n_s, params->sigma8);
+  for (int k = 0; k < 12; ++k) out[k] = 0.0;
+  if (i == 0) {
+    const double a1 = 1.0 / params->nstep;
+    out[0] = a1;
+    out[8] = cosmo.d1_da(1.0) * hubble(1.0, params->omega_m);
+    out[9] = cosmo.d2_da(1.0) * hubble(1.0, params->omega_m);
+    out[10] = cosmo.d1(a1);
+    out[11] = cosmo.d2(a1);
+    return COLA_OK;
+  }
+  const StepScalars s = step_scalars(*params, cosmo, i);
+  const double v[12] = {s.a, s.a_lo, s.a_hi, s.force_scale, s.c1, s.c2, s.kick, s.drift, s.dd1, s.dd2, s.d1, s.d2};
+  for (int k = 0; k < 12; ++k) out[k] = v[k];
+  return COLA_OK;
+}
+
+extern "C" void cola_destroy(cola_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  if (c->edges_host) cudaFreeHost(c->edges_host);
+  fft_plan_free(&c->mplan);
+  fft_plan_free(&c->lplan);
+  void* bufs[] = {c->arena, c->dtab, c->amp_m2, c->edges, c->pk_partials, c->flags};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  delete c;
+}
+
+extern "C" int cola_create(const cola_params* params, void* stream, cola_ctx** out) {
+  if (!out) return COLA_ERR_INVALID;
+  *out = nullptr;
+  COLA_TRY(validate(params));
+  cola_ctx* c = new (std::nothrow) cola_ctx;
+  if (!c) return COLA_ERR_OOM;
+  c->p = *params;
+  c->stream = static_cast<cudaStream_t>(stream);
+  c->mesh = make_grid(params->nmesh);
+  c->lat = make_grid(params->np);
+  c->pg.np = params->np;
+  c->pg.n = params->nmesh;
+  c->pg.r_fixed = (((long long)params->nmesh) << 20) / params->np;
+  c->pg.npart = (long long)params->np * params->np * params->np;
+  auto fail = [&](int st) {
+    cola_destroy(c);
+    return st;
+  };
+  int st = fft_plan_init(&c->mplan, params->nmesh);
+  if (st == COLA_OK) st = fft_plan_init(&c->lplan, params->np);
+  if (st != COLA_OK) return fail(st);
+
+  // host FP64 tables
+  const Cosmo cosmo(params->omega_m, params->h, params->n_s, params->sigma8);
+  c->steps.resize(params->nstep + 1);
+  for (int i = 1; i <= params->nstep; ++i) c->steps[i] = step_scalars(*params, cosmo, i);
+  {
+    const double a1 = 1.0 / params->nstep;
+    c->steps[0] = StepScalars{};
+    c->steps[0].a = a1;
+    c->steps[0].d1 = cosmo.d1(a1);
+    c->steps[0].d2 = cosmo.d2(a1);
+    c->vel_f1 = cosmo.d1_da(1.0) * hubble(1.0, params->omega_m);
+    c->vel_f2 = cosmo.d2_da(1.0) * hubble(1.0, params->omega_m);
+  }
+
+  // device memory: meshes and the IC work space share one arena
+  const size_t cbytes = align256(c->mesh.complex_elems() * sizeof(float2));
+  const size_t nm3 = (size_t)params->nmesh * params->nmesh * params->nmesh;
+  const size_t mesh_bytes = align256(nm3 * sizeof(unsigned long long)) + 3 * cbytes;
+  const size_t lbytes = align256(c->lat.complex_elems() * sizeof(float2));
+  const size_t ic_bytes = 8 * lbytes;
+  c->arena_bytes = mesh_bytes > ic_bytes ? mesh_bytes : ic_bytes;
+  if ((st = cuda_status(cudaMalloc(&c->arena, c->arena_bytes), "cudaMalloc arena")) != COLA_OK) return fail(st);
+  char* base = static_cast<char*>(c->arena);
+  c->rho = reinterpret_cast<unsigned long long*>(base);
+  for (int j = 0; j < 3; ++j)
+    c->cbuf[j] = reinterpret_cast<float2*>(base + align256(nm3 * sizeof(unsigned long long)) + j * cbytes);
+
+  // gradient kernel per storage index: D(m) = (8 sin k - sin 2k)/6, k = 2 pi m / N, 0 at Nyquist
+  {
+    const int n = params->nmesh;
+    std::vector<float> d(n);
+    for (int j = 0; j < n; ++j) {
+      const int m = j < n / 2 ? j : j - n;
+      const double k = 2.0 * M_PI * m / n;
+      d[j] = (2 * j == n) ? 0.0f : (float)((8.0 * std::sin(k) - std::sin(2.0 * k)) / 6.0);
+    }
+    if ((st = cuda_status(cudaMalloc(&c->dtab, n * sizeof(float)), "cudaMalloc dtab")) != COLA_OK) return fail(st);
+    cudaMemcpy(c->dtab, d.data(), n * sizeof(float), cudaMemcpyHostToDevice);
+  }
+  // sqrt(P(k) / V_cell) / np^3 per integer |m|^2 of the lattice, k = 2 pi |m| / L
+  {
+    const int npd = params->np;
+    const long long m2max = 3LL * (npd / 2) * (npd / 2);
+    std::vector<float> amp(m2max + 1);
+    const double vcell = std::pow(params->box / npd, 3);
+    const double n3 = (double)npd * npd * npd;
+    amp[0] = 0.0f;
+    for (long long m2 = 1; m2 <= m2max; ++m2) {
+      const double k = 2.0 * M_PI * std::sqrt((double)m2) / params->box;
+      amp[m2] = (float)(std::sqrt(cosmo.power(k) / vcell) / n3);
+    }
+    if ((st = cuda_status(cudaMalloc(&c->amp_m2, amp.size() * sizeof(float)), "cudaMalloc amp")) != COLA_OK)
+      return fail(st);
+    cudaMemcpy(c->amp_m2, amp.data(), amp.size() * sizeof(float), cudaMemcpyHostToDevice);
+  }
+  c->pk_blocks = kPkBlocks;
+  if ((st = cuda_status(cudaMalloc(&c->edges, (kPkMaxBins + 1) * sizeof(long long)), "cudaMalloc")) != COLA_OK ||
+      (st = cuda_status(cudaMalloc(&c->pk_partials, (size_t)kPkBlocks * 3 * kPkMaxBins * sizeof(double)),
+                        "cudaMalloc")) != COLA_OK ||
+      (st = cuda_status(cudaMalloc(&c->flags, sizeof(int)), "cudaMalloc")) != COLA_OK)
+    return fail(st);
+  cudaMemset(c->flags, 0, sizeof(int));
+  if ((st = cuda_status(cudaMallocHost(&c->edges_host, (kPkMaxBins + 1) * sizeof(long long)), "cudaMallocHost")) !=
+      COLA_OK)
+    return fail(st);
+  bin_edges(params->nmesh, 64, c->edges_host);
+  c->edges_nbins = 64;
+  cudaMemcpy(c->edges, c->edges_host, 65 * sizeof(long long), cudaMemcpyHostToDevice);
+  if ((st = cuda_status(cudaDeviceSynchronize(), "create")) != COLA_OK) return fail(st);
+  *out = c;
+  return COLA_OK;
+}
+
+extern "C" int cola_sync(cola_ctx* c) {
+  if (!c) return COLA_ERR_INVALID;
+  COLA_TRY(cuda_status(cudaStreamSynchronize(c->stream), "stream sync"));
+  int flags = 0;
+  COLA_TRY(cuda_status(cudaMemcpy(&flags, c->flags, sizeof(int), cudaMemcpyDeviceToHost), "flags"));
+  if (flags) cudaMemset(c->flags, 0, sizeof(int));
+  if (flags & 1) return COLA_ERR_OVERFLOW;
+  if (flags & 2) return COLA_ERR_NONFINITE;
+  return COLA_OK;
+}
+
+extern "C" int cola_ic_2lpt(cola_ctx* c, const float* wn, float* s, float* v, float* psi1, float* psi2) {
+  if (!c) return COLA_ERR_INVALID;
+  for (const void* p : {(const void*)wn, (const void*)s, (const void*)v, (const void*)psi1, (const void*)psi2})
+    COLA_TRY(check_ptr(p));
+  const Grid3& g = c->lat;
+  const FftPlan& P = c->lplan;
+  const size_t lbytes = align256(g.complex_elems() * sizeof(float2));
+  float2* B[8];
+  for (int i = 0; i < 8; ++i) B[i] = reinterpret_cast<float2*>(static_cast<char*>(c->arena) + i * lbytes);
+  const long long n = c->pg.npart;
+  const float r = (float)c->p.nmesh / (float)c->p.np;   // lattice spacings -> mesh cells
+  // white noise -> W(k) -> delta_L(k) / np^3
+  COLA_TRY(launch_r2c_rows(P, g, kSrcFloat, wn, g.n, 1.0f, B[0], c->stream));
+  COLA_TRY(forward3d_yx(c, g, P, B[0]));
+  COLA_TRY(launch_ic_amplitude(g, B[0], c->amp_m2, c->stream));
+  // Psi1 = i k delta_L / k^2
+  for (int j = 0; j < 3; ++j) {
+    COLA_TRY(launch_ic_multiply(g, B[0], B[7], kIcPsi1, j, 0, 1.0f, c->stream));
+    COLA_TRY(inverse3d(c, g, P, B[7]));
+    COLA_TRY(launch_ic_to_particles(g, B[7], r, psi1 + j * n, c->stream));
+  }
+  // phi1_ij = k_i k_j delta_L / k^2 in real space, then the second-order source
+  const int pairs[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
+  for (int h = 0; h < 6; ++h) {
+    COLA_TRY(launch_ic_multiply(g, B[0], B[1 + h], kIcHess, pairs[h][0], pairs[h][1], 1.0f, c->stream));
+    COLA_TRY(inverse3d(c, g, P, B[1 + h]));
+  }
+  float2* const hs[6] = {B[1], B[2], B[3], B[4], B[5], B[6]};
+  COLA_TRY(launch_ic_source(g, hs, B[7], c->stream));
+  COLA_TRY(launch_r2c_rows(P, g, kSrcFloat, B[7], 2LL * g.pc, 1.0f, B[7], c->stream));
+  COLA_TRY(forward3d_yx(c, g, P, B[7]));
+  // Psi2 = -i k S(k) / k^2
+  const float inv_n3 = (float)(1.0 / ((double)g.n * g.n * g.n));
+  for (int j = 0; j < 3; ++j) {
+    COLA_TRY(launch_ic_multiply(g, B[7], B[1], kIcPsi2, j, 0, inv_n3, c->stream));
+    COLA_TRY(inverse3d(c, g, P, B[1]));
+    COLA_TRY(launch_ic_to_particles(g, B[1], r, psi2 + j * n, c->stream));
+  }
+  const StepScalars& s0 = c->steps[0];
+  return launch_ic_positions(n, psi1, psi2, (float)s0.d1, (float)s0.d2, s, v, c->stream);
+}
+
+extern "C" int cola_deposit(cola_ctx* c, const float* s, unsigned long long* rho) {
+  if (!c) return COLA_ERR_INVALID;
+  COLA_TRY(check_ptr(s));
+  COLA_TRY(check_ptr(rho));
+  const size_t n3 = (size_t)c->mesh.n * c->mesh.n * c->mesh.n;
+  COLA_TRY(cuda_status(cudaMemsetAsync(rho, 0, n3 * sizeof(unsigned long long), c->stream), "memset"));
+  return launch_deposit(c->pg, s, rho, c->flags, c->stream);
+}
+
+extern "C" int cola_density_spectrum(cola_ctx* c, const float* s, float* delta_k) {
+  if (!c) return COLA_ERR_INVALID;
+  COLA_TRY(check_ptr(s));
+  COLA_TRY(check_ptr(delta_k));
+  COLA_TRY(deposit_and_forward_yz(c, s));
+  COLA_TRY(launch_pencils(c->mplan, c->mesh, 0, -1, c->cbuf[2], c->stream));
+  return launch_dense_spectrum(c->mesh, c->cbuf[2], delta_k, c->stream);
+}
+
+extern "C" int cola_pm_force(cola_ctx* c, const float* s, double a, float* force) {
+  if (!c || !(a > 0.0)) return COLA_ERR_INVALID;
+  COLA_TRY(check_ptr(s));
+  COLA_TRY(check_ptr(force));
+  COLA_TRY(force_mesh(c, s, 1.5 * c->p.omega_m / a));
+  const float* f[3] = {reinterpret_cast<float*>(c->cbuf[0]), reinterpret_cast<float*>(c->cbuf[1]),
+                       reinterpret_cast<float*>(c->cbuf[2])};
+  return launch_gather(c->pg, f, 2LL * c->mesh.pc, s, force, nullptr, nullptr, nullptr, nullptr, nullptr,
+                       c->flags, c->stream);
+}
+
+extern "C" int cola_step(cola_ctx* c, int i, float* s, float* v, const float* psi1, const float* psi2) {
+  if (!c || i < 1 || i > c->p.nstep) return COLA_ERR_INVALID;
+  for (const void* p : {(const void*)s, (const void*)v, (const void*)psi1, (const void*)psi2})
+    COLA_TRY(check_ptr(p));
+  const StepScalars& ss = c->steps[i];
+  COLA_TRY(force_mesh(c, s, ss.force_scale));
+  const KickDrift kd{(float)ss.kick, (float)ss.drift, (float)ss.dd1, (float)ss.dd2, (float)ss.c1, (float)ss.c2};
+  const float* f[3] = {reinterpret_cast<float*>(c->cbuf[0]), reinterpret_cast<float*>(c->cbuf[1]),
+                       reinterpret_cast<float*>(c->cbuf[2])};
+  return launch_gather(c->pg, f, 2LL * c->mesh.pc, nullptr, nullptr, s, v, psi1, psi2, &kd, c->flags, c->stream);
+}
+
+extern "C" int cola_power_spectrum(cola_ctx* c, const float* s, double* pk, int nbins) {
+  if (!c || nbins < 1 || nbins > kPkMaxBins) return COLA_ERR_INVALID;
+  COLA_TRY(check_ptr(s));
+  COLA_TRY(check_ptr(pk));
+  if (nbins != c->edges_nbins) {
+    // the pinned host copy may still feed an earlier upload: wait for it before rewriting it
+    COLA_TRY(cuda_status(cudaStreamSynchronize(c->stream), "pk edges"));
+    bin_edges(c->mesh.n, nbins, c->edges_host);
+    COLA_TRY(cuda_status(cudaMemcpyAsync(c->edges, c->edges_host, (nbins + 1) * sizeof(long long),
+                                         cudaMemcpyHostToDevice, c->stream), "edges"));
+    c->edges_nbins = nbins;
+  }
+  COLA_TRY(deposit_and_forward_yz(c, s));
+  COLA_TRY(launch_pencils(c->mplan, c->mesh, 0, -1, c->cbuf[2], c->stream));
+  const double nn = c->mesh.n;
+  const double pscale = std::pow(c->p.box, 3) / (nn * nn * nn * nn * nn * nn);
+  const double kfund = 2.0 * M_PI / c->p.box;
+  COLA_TRY(launch_pk_bins(c->mesh, c->cbuf[2], c->edges, nbins, pscale, kfund, c->pk_partials, c->pk_blocks,
+                          c->stream));
+  return launch_pk_finish(c->pk_partials, c->pk_blocks, nbins, pk, c->stream);
+}
+
+extern "C" int cola_run(cola_ctx* c, const float* wn, float* s, float* v, float* psi1, float* psi2, double* pk,
+                        int nbins) {
+  if (!c) return COLA_ERR_INVALID;
+  COLA_TRY(cola_ic_2lpt(c, wn, s, v, psi1, psi2));
+  for (int i = 1; i <= c->p.nstep; ++i) COLA_TRY(cola_step(c, i, s, v, psi1, psi2));
+  if (pk) COLA_TRY(cola_power_spectrum(c, s, pk, nbins));
+  return COLA_OK;
+}

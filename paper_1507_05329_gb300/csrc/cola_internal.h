@@ -1,0 +1,151 @@
+// Internal declarations shared by the library's translation units (host-visible only).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <vector>
+
+#include "../../include/cola.h"
+
+namespace cola {
+
+double hubble(double a, double om);
+
+// FP64 background cosmology and linear power (host only).
+struct Cosmo {
+  double om, h, ns, sigma8;
+  double i1 = 0.0;   // growth integral at a = 1
+  double amp = 0.0;  // P(k) amplitude A from sigma8
+  Cosmo(double om, double h, double ns, double sigma8);
+  double transfer(double k) const;
+  double power(double k) const;
+  double omega_a(double a) const;
+  double d1(double a) const;
+  double d1_da(double a) const;
+  double d2(double a) const;
+  double d2_da(double a) const;
+  double drift(double a0, double a1, double ahalf, double nlpt, int ansatz) const;
+  double kick(double alo, double ahi, double ai, double nlpt) const;
+};
+
+struct StepScalars {
+  double a, a_lo, a_hi, force_scale, c1, c2, kick, drift, dd1, dd2, d1, d2;
+};
+
+StepScalars step_scalars(const cola_params& p, const Cosmo& c, int i);
+
+// ---------------------------------------------------------------------------------------------
+// FFT plan: one transform length, its radix stages and the twiddle table exp(-2 pi i t / n).
+// ---------------------------------------------------------------------------------------------
+constexpr int kMaxStages = 12;
+
+struct FftDev {
+  int n;
+  int nstages;
+  int radix[kMaxStages];
+  const float2* tw;   // device table, n entries
+};
+
+struct FftPlan {
+  FftDev dev{};
+  float2* tw = nullptr;   // owned device memory
+  int w_pencil = 8;       // pencils per CTA in the strided passes
+  int w_rows = 4;         // row pairs per CTA in the contiguous (R2C / C2R) passes
+  int ept = 16;           // complex elements per thread
+};
+
+// Factor n into radices {16, 8, 5, 4, 3, 2}; returns false if n has another prime factor.
+bool fft_factor(int n, std::vector<int>* radices);
+int fft_plan_init(FftPlan* plan, int n);   // allocates the twiddle table; returns cola_status
+void fft_plan_free(FftPlan* plan);
+
+// Geometry of a 3D field of side n in the in-place real-to-complex layout:
+// complex rows of pc = (n/2+1 rounded up to even) entries, real rows of 2*pc floats.
+struct Grid3 {
+  int n;
+  int nc;            // n/2 + 1 valid complex entries per row
+  int pc;            // padded complex row length
+  size_t rows() const { return (size_t)n * n; }
+  size_t complex_elems() const { return rows() * pc; }
+};
+
+// Sources of the contiguous-axis forward transform.
+enum RowSource { kSrcFixedPoint = 0, kSrcFloat = 1 };
+
+// Launchers (fft.cu).  All take the stream explicitly.
+// Forward R2C along z of n^2 rows; src is uint64 (scaled: value*scale - 1) or float rows with
+// the given row stride (floats or uint64 elements).  dst: complex grid rows of stride pc.
+int launch_r2c_rows(const FftPlan& p, const Grid3& g, RowSource kind, const void* src,
+                    long long src_row_stride, float scale, float2* dst, cudaStream_t st);
+// Inverse C2R along z, in place on a complex grid (real rows of stride 2*pc floats).
+int launch_c2r_rows(const FftPlan& p, const Grid3& g, float2* data, cudaStream_t st);
+// C2C along y (axis 1) or x (axis 0) of the complex grid; dir = -1 forward, +1 inverse.
+int launch_pencils(const FftPlan& p, const Grid3& g, int axis, int dir, float2* data,
+                   cudaStream_t st);
+// Forward x transform, then for each j in {x, y, z}: out_j = i D(k_j) scale delta(k)/k^2
+// (k in rad/cell, D the 4-point gradient kernel), then the inverse x transform of out_j.
+// out[2] may alias in.
+int launch_green_x(const FftPlan& p, const Grid3& g, const float2* in, float2* const out[3],
+                   const float* dtab, float scale, cudaStream_t st);
+
+// Launchers (particles.cu).
+struct ParticleGeom {
+  int np;             // particles per side
+  int n;              // mesh cells per side
+  long long r_fixed;  // (n/np) * 2^20
+  long long npart;    // np^3
+};
+
+int launch_deposit(const ParticleGeom& pg, const float* s, unsigned long long* rho, int* flags,
+                   cudaStream_t st);
+struct KickDrift {
+  float kick, drift, dd1, dd2, c1, c2;
+};
+// Interpolates the three real force fields (rows of stride rs floats) at the particles; with
+// kd == nullptr writes the force to out[3][n], else applies the COLA kick and drift in place.
+int launch_gather(const ParticleGeom& pg, const float* const f[3], long long rs, const float* s_in,
+                  float* force_out, float* s, float* v, const float* psi1, const float* psi2,
+                  const KickDrift* kd, int* flags, cudaStream_t st);
+
+// 2LPT helpers on the lattice grid (side np).
+enum IcField { kIcPsi1 = 0, kIcHess = 1, kIcPsi2 = 2 };
+int launch_ic_amplitude(const Grid3& g, float2* wk, const float* amp_m2, cudaStream_t st);
+int launch_ic_multiply(const Grid3& g, const float2* src, float2* dst, IcField kind, int i, int j,
+                       float scale, cudaStream_t st);
+int launch_ic_source(const Grid3& g, float2* const h[6], float2* dst, cudaStream_t st);
+int launch_ic_to_particles(const Grid3& g, const float2* field, float scale, float* dst,
+                           cudaStream_t st);
+int launch_ic_positions(long long npart, const float* psi1, const float* psi2, float d1, float d2,
+                        float* s, float* v, cudaStream_t st);
+
+// Power spectrum binning of a forward spectrum (side n).
+int launch_pk_bins(const Grid3& g, const float2* dk, const long long* edges, int nbins,
+                   double pscale, double kfund, double* partials, int nblocks, cudaStream_t st);
+int launch_pk_finish(const double* partials, int nblocks, int nbins, double* pk, cudaStream_t st);
+int launch_dense_spectrum(const Grid3& g, const float2* src, float* dst, cudaStream_t st);
+
+}  // namespace cola
+
+// The context (cola_abi.cu).
+struct cola_ctx {
+  cola_params p;
+  cudaStream_t stream = nullptr;
+  cola::Grid3 mesh{}, lat{};
+  cola::FftPlan mplan, lplan;
+  cola::ParticleGeom pg{};
+  std::vector<cola::StepScalars> steps;   // index 1..nstep; [0] holds initial-condition scalars
+  double vel_f1 = 0.0, vel_f2 = 0.0;      // a^2 dD/dt at a = 1
+  // device memory
+  void* arena = nullptr;                  // meshes (and the IC work space, aliased)
+  size_t arena_bytes = 0;
+  unsigned long long* rho = nullptr;      // [N^3]
+  float2* cbuf[3] = {nullptr, nullptr, nullptr};   // complex N x N x pc each
+  float* dtab = nullptr;                  // gradient kernel per storage index, N entries
+  float* amp_m2 = nullptr;                // sqrt(P(k)/V_cell) per integer m^2 of the lattice
+  long long* edges = nullptr;             // P(k) bin edges in m^2 (device), up to 129
+  long long* edges_host = nullptr;        // pinned host copy of the current edges
+  int edges_nbins = 0;
+  double* pk_partials = nullptr;
+  int pk_blocks = 0;
+  int* flags = nullptr;                   // sticky device error flags
+};

@@ -1,0 +1,417 @@
+// Particle-side kernels of the COLA step (sm_103a): CIC deposit, CIC gather fused with the COLA
+// kick and drift, the 2LPT initial-condition helpers, and the power-spectrum binning.
+//
+//   deposit ............ §2.3 PM mesh, §3.3 CIC; deterministic 64-bit fixed point (exact sums)
+//   gather/kick/drift .. §2.1 residual force F_res = F - F_2LPT; §2.2 eqs. (cola-kick), (cola-drift)
+//   2LPT ............... §2.1 growing mode x = q + D1 Psi1 + D2 Psi2; §2.3 2LPTic-style fields
+//   P(k) ............... §3.3 half-space modes and bin averages
+#include "cola_internal.h"
+
+#include <cstdio>
+
+namespace cola {
+namespace {
+
+constexpr int kFracBits = 20;
+constexpr long long kFracOne = 1LL << kFracBits;
+constexpr int kWeightOne = 1 << 14;
+
+int check_launch(const char* what) {
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    std::fprintf(stderr, "cola: launch of %s failed: %s\n", what, cudaGetErrorString(e));
+    return COLA_ERR_CUDA;
+  }
+  return COLA_OK;
+}
+
+unsigned grid_for(long long work, int threads) {
+  long long b = (work + threads - 1) / threads;
+  const long long cap = 152LL * 16 * 4;   // enough resident CTAs; kernels grid-stride beyond it
+  if (b > cap) b = cap;
+  return (unsigned)(b < 1 ? 1 : b);
+}
+
+// Fixed-point mesh coordinate of one axis: G = (q R + rint(s 2^20)) mod (N 2^20).
+__device__ __forceinline__ long long fixed_coord(int q, float s, long long r_fixed, long long modulus) {
+  long long g = (long long)q * r_fixed + __float2ll_rn(s * (float)kFracOne);
+  g %= modulus;
+  return g < 0 ? g + modulus : g;
+}
+
+__device__ __forceinline__ void lattice_index(long long id, int np, int* qx, int* qy, int* qz) {
+  const long long np2 = (long long)np * np;
+  *qx = (int)(id / np2);
+  const long long rem = id - (long long)(*qx) * np2;
+  *qy = (int)(rem / np);
+  *qz = (int)(rem - (long long)(*qy) * np);
+}
+
+__global__ void k_deposit(ParticleGeom pg, const float* __restrict__ s, unsigned long long* rho,
+                          int* flags) {
+  const long long n = pg.npart;
+  const long long modulus = (long long)pg.n << kFracBits;
+  const long long nm = pg.n;
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < n;
+       id += (long long)gridDim.x * blockDim.x) {
+    int q[3];
+    lattice_index(id, pg.np, &q[0], &q[1], &q[2]);
+    long long c[3];
+    unsigned long long w1[3], w0[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const long long g = fixed_coord(q[a], s[a * n + id], pg.r_fixed, modulus);
+      c[a] = g >> kFracBits;
+      w1[a] = (unsigned long long)((g >> (kFracBits - 14)) & (kWeightOne - 1));
+      w0[a] = kWeightOne - w1[a];
+    }
+    bool over = false;
+#pragma unroll
+    for (int dx = 0; dx < 2; ++dx) {
+      const long long ix = (c[0] + dx) == nm ? 0 : c[0] + dx;
+#pragma unroll
+      for (int dy = 0; dy < 2; ++dy) {
+        const long long iy = (c[1] + dy) == nm ? 0 : c[1] + dy;
+        const unsigned long long wxy = (dx ? w1[0] : w0[0]) * (dy ? w1[1] : w0[1]);
+        unsigned long long* row = rho + (ix * nm + iy) * nm;
+#pragma unroll
+        for (int dz = 0; dz < 2; ++dz) {
+          const long long iz = (c[2] + dz) == nm ? 0 : c[2] + dz;
+          const unsigned long long w = wxy * (dz ? w1[2] : w0[2]);
+          if (w) {
+            const unsigned long long old = atomicAdd(row + iz, w);
+            over |= (old + w < old);
+          }
+        }
+      }
+    }
+    if (over) atomicOr(flags, 1);
+  }
+}
+
+// CIC gather of the three force fields, optionally fused with the COLA kick and drift.
+template <bool KICK>
+__global__ void k_gather(ParticleGeom pg, const float* __restrict__ f0, const float* __restrict__ f1,
+                         const float* __restrict__ f2, long long rs, const float* __restrict__ s_in,
+                         float* __restrict__ force_out, float* s, float* v, const float* __restrict__ psi1,
+                         const float* __restrict__ psi2, KickDrift kd, int* flags) {
+  const long long n = pg.npart;
+  const long long modulus = (long long)pg.n << kFracBits;
+  const long long nm = pg.n;
+  const float inv_one = 1.0f / kWeightOne;
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < n;
+       id += (long long)gridDim.x * blockDim.x) {
+    int q[3];
+    lattice_index(id, pg.np, &q[0], &q[1], &q[2]);
+    const float* sp = KICK ? s : s_in;
+    float sv[3];
+    long long c[3];
+    float w1[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      sv[a] = sp[a * n + id];
+      const long long g = fixed_coord(q[a], sv[a], pg.r_fixed, modulus);
+      c[a] = g >> kFracBits;
+      w1[a] = (float)((g >> (kFracBits - 14)) & (kWeightOne - 1)) * inv_one;
+    }
+    float fx = 0.f, fy = 0.f, fz = 0.f;
+#pragma unroll
+    for (int dx = 0; dx < 2; ++dx) {
+      const long long ix = (c[0] + dx) == nm ? 0 : c[0] + dx;
+      const float wx = dx ? w1[0] : 1.0f - w1[0];
+#pragma unroll
+      for (int dy = 0; dy < 2; ++dy) {
+        const long long iy = (c[1] + dy) == nm ? 0 : c[1] + dy;
+        const float wxy = wx * (dy ? w1[1] : 1.0f - w1[1]);
+        const long long row = (ix * nm + iy) * rs;
+#pragma unroll
+        for (int dz = 0; dz < 2; ++dz) {
+          const long long iz = (c[2] + dz) == nm ? 0 : c[2] + dz;
+          const float w = wxy * (dz ? w1[2] : 1.0f - w1[2]);
+          fx += w * __ldg(f0 + row + iz);
+          fy += w * __ldg(f1 + row + iz);
+          fz += w * __ldg(f2 + row + iz);
+        }
+      }
+    }
+    if (!KICK) {
+      force_out[id] = fx;
+      force_out[n + id] = fy;
+      force_out[2 * n + id] = fz;
+    } else {
+      const float fp[3] = {fx, fy, fz};
+      bool bad = false;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const float p1 = psi1[a * n + id], p2 = psi2[a * n + id];
+        const float fres = fp[a] - (kd.c1 * p1 + kd.c2 * p2);
+        const float vn = v[a * n + id] + kd.kick * fres;
+        const float sn = sv[a] + kd.drift * vn + kd.dd1 * p1 + kd.dd2 * p2;
+        v[a * n + id] = vn;
+        s[a * n + id] = sn;
+        bad |= !isfinite(vn) || !isfinite(sn);
+      }
+      if (bad) atomicOr(flags, 2);
+    }
+  }
+}
+
+// ---- 2LPT helpers on the lattice grid (side n = np, half spectrum rows of pc) --------------
+__device__ __forceinline__ int signed_mode(int i, int n) { return i < n / 2 ? i : i - n; }
+
+__global__ void k_ic_amplitude(int n, int pc, int nc, float2* wk, const float* __restrict__ amp_m2) {
+  const long long total = (long long)n * n * nc;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int kz = (int)(t % nc);
+    const long long row = t / nc;
+    const int my = signed_mode((int)(row % n), n), mx = signed_mode((int)(row / n), n);
+    const long long m2 = (long long)mx * mx + (long long)my * my + (long long)kz * kz;
+    float2 z = wk[row * pc + kz];
+    const float a = amp_m2[m2];
+    wk[row * pc + kz] = make_float2(z.x * a, z.y * a);
+  }
+}
+
+// dst(k) = M(k) src(k): Psi1 component i: i kodd_i / k^2; Hessian (i, j): k_i k_j / k^2 (diagonal
+// uses the full k_i, off-diagonal the Nyquist-zeroed kodd); Psi2 component i: -i kodd_i / k^2.
+// k in radians per lattice spacing, times 'scale'.
+__global__ void k_ic_multiply(int n, int pc, int nc, const float2* __restrict__ src, float2* dst, int kind,
+                              int ci, int cj, float scale) {
+  const long long total = (long long)n * n * nc;
+  const float kf = 6.283185307179586f / n;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int kz = (int)(t % nc);
+    const long long row = t / nc;
+    int m[3] = {signed_mode((int)(row / n), n), signed_mode((int)(row % n), n), kz};
+    const float m2 = (float)m[0] * m[0] + (float)m[1] * m[1] + (float)m[2] * m[2];
+    const float2 z = src[row * pc + kz];
+    float2 out = make_float2(0.f, 0.f);
+    if (m2 > 0.f) {
+      const float inv_k2 = 1.0f / (m2 * kf * kf);
+      const int nyq = n / 2;
+      const float koi = (m[ci] == nyq || m[ci] == -nyq) ? 0.f : m[ci] * kf;
+      if (kind == kIcPsi1) {
+        const float c = koi * inv_k2 * scale;              // i c z
+        out = make_float2(-c * z.y, c * z.x);
+      } else if (kind == kIcPsi2) {
+        const float c = -koi * inv_k2 * scale;
+        out = make_float2(-c * z.y, c * z.x);
+      } else {
+        float kk;
+        if (ci == cj) kk = (m[ci] * kf) * (m[ci] * kf);
+        else {
+          const float koj = (m[cj] == nyq || m[cj] == -nyq) ? 0.f : m[cj] * kf;
+          kk = koi * koj;
+        }
+        const float c = kk * inv_k2 * scale;
+        out = make_float2(c * z.x, c * z.y);
+      }
+    }
+    dst[row * pc + kz] = out;
+  }
+}
+
+// S = h00 h11 + h00 h22 + h11 h22 - h01^2 - h02^2 - h12^2 on real rows of stride 2 pc.
+__global__ void k_ic_source(int n, int pc, const float* __restrict__ h0, const float* __restrict__ h1,
+                            const float* __restrict__ h2, const float* __restrict__ h3,
+                            const float* __restrict__ h4, const float* __restrict__ h5, float* dst) {
+  const long long total = (long long)n * n * n;
+  const long long rs = 2LL * pc;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long i = (t / n) * rs + (t % n);
+    const float a = h0[i], b = h1[i], c = h2[i], d = h3[i], e = h4[i], f = h5[i];
+    dst[i] = a * b + a * c + b * c - d * d - e * e - f * f;
+  }
+}
+
+__global__ void k_ic_to_particles(int n, int pc, const float* __restrict__ field, float scale, float* dst) {
+  const long long total = (long long)n * n * n;
+  const long long rs = 2LL * pc;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x)
+    dst[t] = field[(t / n) * rs + (t % n)] * scale;
+}
+
+__global__ void k_ic_positions(long long n3, const float* __restrict__ psi1, const float* __restrict__ psi2,
+                               float d1, float d2, float* s, float* v) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n3;
+       t += (long long)gridDim.x * blockDim.x) {
+    s[t] = d1 * psi1[t] + d2 * psi2[t];
+    v[t] = 0.0f;
+  }
+}
+
+// ---- power spectrum ------------------------------------------------------------------------
+constexpr int kPkThreads = 256;
+constexpr int kPkWarps = kPkThreads / 32;
+constexpr int kMaxBins = 128;
+
+// Each warp walks whole k_z rows; along a row |m|^2 grows with k_z, so equal bins are contiguous
+// runs of lanes.  The lowest lane of a run adds the run's values in lane order into the warp's
+// own histogram; warps and blocks are then summed in index order: a fixed reduction order.
+__global__ void __launch_bounds__(kPkThreads) k_pk_bins(int n, int pc, int nc, const float2* __restrict__ dk,
+                                                        const long long* __restrict__ edges_g, int nbins,
+                                                        double pscale, double kfund, double* partials) {
+  __shared__ long long edges[kMaxBins + 1];
+  __shared__ double hp[kPkWarps][kMaxBins];
+  __shared__ double hk[kPkWarps][kMaxBins];
+  __shared__ long long hc[kPkWarps][kMaxBins];
+  __shared__ double stp[kPkWarps][32], stk[kPkWarps][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i <= nbins; i += blockDim.x) edges[i] = edges_g[i];
+  for (int i = threadIdx.x; i < kPkWarps * kMaxBins; i += blockDim.x) {
+    (&hp[0][0])[i] = 0.0;
+    (&hk[0][0])[i] = 0.0;
+    (&hc[0][0])[i] = 0;
+  }
+  __syncthreads();
+  const long long nrows = (long long)n * n;
+  for (long long row = (long long)blockIdx.x * kPkWarps + warp; row < nrows;
+       row += (long long)gridDim.x * kPkWarps) {
+    const int mx = signed_mode((int)(row / n), n), my = signed_mode((int)(row % n), n);
+    for (int kz0 = 0; kz0 < nc; kz0 += 32) {
+      const int kz = kz0 + lane;
+      int bin = -1;
+      double p = 0.0, kk = 0.0;
+      if (kz < nc) {
+        const bool half = kz > 0 || my > 0 || (my == 0 && mx > 0);
+        const long long m2 = (long long)mx * mx + (long long)my * my + (long long)kz * kz;
+        if (half && m2 >= edges[0] && m2 < edges[nbins]) {
+          int lo = 0, hi = nbins;   // edges[lo] <= m2 < edges[hi]
+          while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (m2 >= edges[mid]) lo = mid; else hi = mid;
+          }
+          bin = lo;
+          const float2 z = dk[row * pc + kz];
+          p = ((double)z.x * z.x + (double)z.y * z.y) * pscale;
+          kk = sqrt((double)m2) * kfund;
+        }
+      }
+      const unsigned grp = __match_any_sync(0xffffffffu, bin);
+      stp[warp][lane] = p;
+      stk[warp][lane] = kk;
+      __syncwarp();
+      if (bin >= 0 && lane == __ffs(grp) - 1) {
+        double sp = 0.0, sk = 0.0;
+        for (unsigned m = grp; m; m &= m - 1) {
+          const int l = __ffs(m) - 1;
+          sp += stp[warp][l];
+          sk += stk[warp][l];
+        }
+        hp[warp][bin] += sp;
+        hk[warp][bin] += sk;
+        hc[warp][bin] += __popc(grp);
+      }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < nbins; b += blockDim.x) {
+    double sp = 0.0, sk = 0.0;
+    long long sc = 0;
+    for (int w = 0; w < kPkWarps; ++w) {
+      sp += hp[w][b];
+      sk += hk[w][b];
+      sc += hc[w][b];
+    }
+    double* out = partials + (size_t)blockIdx.x * 3 * nbins;
+    out[b] = sk;
+    out[nbins + b] = sp;
+    out[2 * nbins + b] = (double)sc;
+  }
+}
+
+__global__ void k_pk_finish(const double* __restrict__ partials, int nblocks, int nbins, double* pk) {
+  for (int b = threadIdx.x; b < nbins; b += blockDim.x) {
+    double sk = 0.0, sp = 0.0, sc = 0.0;
+    for (int i = 0; i < nblocks; ++i) {
+      const double* in = partials + (size_t)i * 3 * nbins;
+      sk += in[b];
+      sp += in[nbins + b];
+      sc += in[2 * nbins + b];
+    }
+    pk[b] = sc > 0 ? sk / sc : 0.0;
+    pk[nbins + b] = sc > 0 ? sp / sc : 0.0;
+    pk[2 * nbins + b] = sc;
+  }
+}
+
+__global__ void k_dense_spectrum(int n, int pc, int nc, const float2* __restrict__ src, float2* dst) {
+  const long long total = (long long)n * n * nc;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x)
+    dst[t] = src[(t / nc) * pc + (t % nc)];
+}
+
+}  // namespace
+
+int launch_deposit(const ParticleGeom& pg, const float* s, unsigned long long* rho, int* flags, cudaStream_t st) {
+  k_deposit<<<grid_for(pg.npart, 256), 256, 0, st>>>(pg, s, rho, flags);
+  return check_launch("deposit");
+}
+
+int launch_gather(const ParticleGeom& pg, const float* const f[3], long long rs, const float* s_in,
+                  float* force_out, float* s, float* v, const float* psi1, const float* psi2,
+                  const KickDrift* kd, int* flags, cudaStream_t st) {
+  const unsigned g = grid_for(pg.npart, 256);
+  if (kd)
+    k_gather<true><<<g, 256, 0, st>>>(pg, f[0], f[1], f[2], rs, nullptr, nullptr, s, v, psi1, psi2, *kd, flags);
+  else
+    k_gather<false><<<g, 256, 0, st>>>(pg, f[0], f[1], f[2], rs, s_in, force_out, nullptr, nullptr, nullptr,
+                                      nullptr, KickDrift{}, flags);
+  return check_launch("gather");
+}
+
+int launch_ic_amplitude(const Grid3& g, float2* wk, const float* amp_m2, cudaStream_t st) {
+  k_ic_amplitude<<<grid_for((long long)g.rows() * g.nc, 256), 256, 0, st>>>(g.n, g.pc, g.nc, wk, amp_m2);
+  return check_launch("ic_amplitude");
+}
+
+int launch_ic_multiply(const Grid3& g, const float2* src, float2* dst, IcField kind, int i, int j, float scale,
+                       cudaStream_t st) {
+  k_ic_multiply<<<grid_for((long long)g.rows() * g.nc, 256), 256, 0, st>>>(g.n, g.pc, g.nc, src, dst, (int)kind,
+                                                                           i, j, scale);
+  return check_launch("ic_multiply");
+}
+
+int launch_ic_source(const Grid3& g, float2* const h[6], float2* dst, cudaStream_t st) {
+  auto f = [](float2* p) { return reinterpret_cast<const float*>(p); };
+  k_ic_source<<<grid_for((long long)g.rows() * g.n, 256), 256, 0, st>>>(
+      g.n, g.pc, f(h[0]), f(h[1]), f(h[2]), f(h[3]), f(h[4]), f(h[5]), reinterpret_cast<float*>(dst));
+  return check_launch("ic_source");
+}
+
+int launch_ic_to_particles(const Grid3& g, const float2* field, float scale, float* dst, cudaStream_t st) {
+  k_ic_to_particles<<<grid_for((long long)g.rows() * g.n, 256), 256, 0, st>>>(
+      g.n, g.pc, reinterpret_cast<const float*>(field), scale, dst);
+  return check_launch("ic_to_particles");
+}
+
+int launch_ic_positions(long long npart, const float* psi1, const float* psi2, float d1, float d2, float* s,
+                        float* v, cudaStream_t st) {
+  k_ic_positions<<<grid_for(3 * npart, 256), 256, 0, st>>>(3 * npart, psi1, psi2, d1, d2, s, v);
+  return check_launch("ic_positions");
+}
+
+int launch_pk_bins(const Grid3& g, const float2* dk, const long long* edges, int nbins, double pscale,
+                   double kfund, double* partials, int nblocks, cudaStream_t st) {
+  k_pk_bins<<<nblocks, kPkThreads, 0, st>>>(g.n, g.pc, g.nc, dk, edges, nbins, pscale, kfund, partials);
+  return check_launch("pk_bins");
+}
+
+int launch_pk_finish(const double* partials, int nblocks, int nbins, double* pk, cudaStream_t st) {
+  k_pk_finish<<<1, 256, 0, st>>>(partials, nblocks, nbins, pk);
+  return check_launch("pk_finish");
+}
+
+int launch_dense_spectrum(const Grid3& g, const float2* src, float* dst, cudaStream_t st) {
+  k_dense_spectrum<<<grid_for((long long)g.rows() * g.nc, 256), 256, 0, st>>>(g.n, g.pc, g.nc, src,
+                                                                              reinterpret_cast<float2*>(dst));
+  return check_launch("dense_spectrum");
+}
+
+}  // namespace cola
