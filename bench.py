@@ -1,0 +1,347 @@
+"""Benchmark of the COLA particle-mesh hot path on GB300.
+
+One step = one whole realisation through the public API (cola_run): 2LPT initial conditions,
+10 COLA PM steps (deposit, FFTs, Poisson + gradient, three inverse FFTs, gather + kick + drift)
+and the P(k) of the final positions.  Default workload: 1024^3 particles, 1536^3 PM mesh,
+L = 1200 Mpc/h (flat LCDM Om=0.27, h=0.7, ns=0.96, sigma8=0.8, BBKS), seeded synthetic white noise.
+Metric: particle-steps/s = (ranks x particles x 10 PM steps) / wall time of one realisation.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
+
+--impl reference times the FP64 CPU oracle (the only reference this method has) on the host cores,
+one oracle PM step per step, on a bounded sample of the same resolution (see SAMPLE).
+With N > 1 (torchrun) every rank runs an independent realisation (different seed, no collective on
+the data path): weak scaling, replicas only.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import cola_inputs  # noqa: E402
+
+METRIC = "particle-steps/s per PM step (whole realisation: 2LPT IC + 10 COLA steps + P(k))"
+UNIT = "particle-steps/s"
+WORKLOADS = {
+    "large": dict(box=1200.0, np_side=1024, nmesh=1536, seed=3),
+    "medium": dict(box=600.0, np_side=256, nmesh=512, seed=2),
+    "small": dict(box=256.0, np_side=32, nmesh=64, seed=1),
+    # the large workload's cell size and r = 1.5 in a 300 Mpc/h box (about 2 GB): ncu captures
+    "profile": dict(box=300.0, np_side=256, nmesh=384, seed=3),
+}
+# CPU oracle sample: same mesh cell (L/N = 0.78 Mpc/h), same r = N/Np = 1.5 as the large workload
+SAMPLE = dict(box=150.0, np_side=128, nmesh=192, seed=3)
+L2_BYTES = 129 * 2 ** 20
+
+
+def describe(w):
+    return (f"{w['np_side']}^3 particles, {w['nmesh']}^3 PM mesh, L={w['box']:g} Mpc/h, 10 COLA steps, "
+            f"seed {w['seed']}")
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    return ws, int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+# ---- algorithmic bytes per launch of each stage (mesh N, particles n) ---------------------------
+def stage_bytes(n_mesh: int, n_part: int) -> dict:
+    nc = n_mesh // 2 + 1
+    cplx = 8.0 * n_mesh * n_mesh * nc          # one complex half-spectrum field
+    real = 4.0 * n_mesh ** 3                   # one real field
+    return {
+        "deposit": 12.0 * n_part + 8.0 * n_mesh ** 3,
+        "fwd_z_r2c": 8.0 * n_mesh ** 3 + cplx,
+        "fwd_y": 2 * cplx,
+        "green_x": cplx + 3 * cplx,
+        "inv_y": 2 * cplx,
+        "inv_z_c2r": cplx + real,
+        "gather_kick_drift": 3 * real + 48.0 * n_part + 24.0 * n_part,
+    }
+
+
+# ---- nvidia-smi clock sampler --------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.lines = []
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.gpu)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---- CPU oracle sample -----------------------------------------------------------------------------
+def oracle_sample_step(repeats: int = 1):
+    """Time one FP64 oracle COLA step on SAMPLE; returns (seconds per step, particles)."""
+    import oracle
+    from oracle import cola, lpt
+    p = oracle.Params(box=SAMPLE["box"], np_side=SAMPLE["np_side"], nmesh=SAMPLE["nmesh"])
+    wn = cola_inputs.white_noise(SAMPLE["np_side"], SAMPLE["seed"])
+    psi1, psi2 = lpt.displacements(wn, p)
+    s, v = cola.initial_state(psi1, psi2, p)
+    times = []
+    for r in range(repeats):
+        t0 = time.perf_counter()
+        s, v = cola.step(1 + r % p.nstep, s, v, psi1, psi2, p)
+        times.append(time.perf_counter() - t0)
+    return times, SAMPLE["np_side"] ** 3
+
+
+def cpu_baseline_entry():
+    times, npart = oracle_sample_step(1)
+    t = times[0]
+    return {"value": npart / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"one FP64 oracle COLA step (numpy, single thread) on {SAMPLE['np_side']}^3 particles / "
+                       f"{SAMPLE['nmesh']}^3 mesh, L={SAMPLE['box']:g} Mpc/h: the large workload's cell size and "
+                       f"particle spacing in a smaller box; {t:.2f} s")}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    w = WORKLOADS[args.workload]
+    times, npart = oracle_sample_step(args.warmup + args.steps)
+    timed = times[args.warmup:]
+    t = sum(timed) / len(timed)
+    value = npart / t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": describe(w), "timed_sample": describe(SAMPLE)},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"one FP64 oracle COLA step per step on {describe(SAMPLE)}"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---- our arm -------------------------------------------------------------------------------------
+def source_digest() -> str:
+    h = hashlib.sha256()
+    for f in ("fft.cu", "particles.cu", "cola_abi.cu", "cola_internal.h"):
+        with open(os.path.join(ROOT, "paper_1507_05329_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(stage: str, workload: str):
+    """DRAM bytes per launch of `stage` from the committed ncu summary, if it was taken on the
+    current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            rec = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    if rec.get("source_digest") != source_digest():
+        return None
+    ent = rec.get("stages", {}).get(stage)
+    if not ent:
+        return None
+    return ent.get("dram_bytes_per_launch_" + workload)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_1507_05329_gb300 import Context, Params, build, binding
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build.build()
+    w = WORKLOADS[args.workload]
+    seed = w["seed"] + 1000 * rank
+    p = Params(box=w["box"], np_side=w["np_side"], nmesh=w["nmesh"], nstep=10)
+    n = p.n
+    stream = torch.cuda.current_stream()
+    ctx = Context(p, stream)
+    wn = cola_inputs.white_noise_torch(p.np_side, seed, f"cuda:{local}")
+    out = {k: ctx.empty_particles() for k in ("s", "v", "psi1", "psi2")}
+    out["pk"] = torch.empty((3, args.nbins), dtype=torch.float64, device=f"cuda:{local}")
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        ctx.run(wn, args.nbins, out=out)
+    ctx.sync()
+
+    sampler = ClockSampler(local)
+    ctx.profile(True)
+    barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.5)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        ctx.run(wn, args.nbins, out=out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    ctx.sync()
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    ms = e0.elapsed_time(e1) / args.steps
+    if ws > 1:
+        t = torch.tensor([ms], device=f"cuda:{local}", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * n * p.nstep / (ms / 1e3)
+
+    # roofline of the dominant PM-step kernel
+    sb = stage_bytes(p.nmesh, n)
+    stages = {k: {"ms_total": v[0], "launches": v[1]} for k, v in prof.items()}
+    pm_stages = [k for k in sb if prof[k][1] > 0]
+    dom = max(pm_stages, key=lambda k: prof[k][0])
+    avg_ms = prof[dom][0] / prof[dom][1]
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peaks = json.load(fh)
+    except (OSError, ValueError):
+        pass
+    peak = peaks.get("hbm_gbs")
+    peak_src = "measured" if peak else "fallback"
+    peak = peak or 6800.0
+    achieved = sb[dom] / (avg_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_src,
+                "traffic": recorded_traffic(dom, args.workload),
+                "algorithmic_bytes_per_launch": sb[dom], "avg_launch_ms": avg_ms}
+    per_stage = {}
+    for k in sb:
+        if prof[k][1]:
+            a = prof[k][0] / prof[k][1]
+            per_stage[k] = {"avg_ms": round(a, 4), "launches": prof[k][1],
+                            "GBps": round(sb[k] / (a / 1e3) / 1e9, 1), "frac": round(sb[k] / (a / 1e3) / 1e9 / peak, 3)}
+    launches = sum(v[1] for k, v in prof.items() if k != "clear")
+    pm_ms = sum(prof[k][0] for k in sb) / args.steps
+
+    # end to end through the public API with host buffers (pinned), copies inside the timed region
+    e2e = None
+    if args.e2e_steps > 0:
+        wn_host = torch.empty(n, dtype=torch.float32, pin_memory=True)
+        wn_host.copy_(wn.cpu())
+        s_host = torch.empty((3, n), dtype=torch.float32, pin_memory=True)
+        v_host = torch.empty((3, n), dtype=torch.float32, pin_memory=True)
+        pk_host = torch.empty((3, args.nbins), dtype=torch.float64, pin_memory=True)
+        wn_dev = torch.empty_like(wn)
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            wn_dev.copy_(wn_host, non_blocking=True)
+            ctx.run(wn_dev, args.nbins, out=out)
+            s_host.copy_(out["s"], non_blocking=True)
+            v_host.copy_(out["v"], non_blocking=True)
+            pk_host.copy_(out["pk"], non_blocking=True)
+            torch.cuda.synchronize()
+        t_e2e = (time.perf_counter() - t0) / args.e2e_steps
+        if ws > 1:
+            t = torch.tensor([t_e2e], device=f"cuda:{local}", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            t_e2e = float(t.item())
+        e2e = {"value": ws * n * p.nstep / t_e2e, "unit": UNIT, "h2d_bytes_per_step": 4 * n,
+               "d2h_bytes_per_step": 24 * n + 24 * args.nbins, "steps": args.e2e_steps,
+               "ms_per_step": t_e2e * 1e3}
+        del wn_host, s_host, v_host, pk_host
+
+    ctx.sync()
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_entry()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32 (int64 fixed-point deposit)", "data": "synthetic",
+                "config": {"workload": describe(w), "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                           "l2": "inputs larger than L2 (no flush needed)",
+                           "pm_step_ms": pm_ms / 10.0, "nbins": args.nbins},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clocks, "stages": per_stage}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="large")
+    ap.add_argument("--nbins", type=int, default=64)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    return run_reference(args) if args.impl == "reference" else run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -53,3 +53,12 @@ def random_field(shape, seed: int) -> np.ndarray:
     """float32 unit Gaussian array of the given shape."""
     rng = np.random.default_rng(seed)
     return rng.standard_normal(shape).astype(np.float32)
+
+
+def white_noise_torch(np_side: int, seed: int, device):
+    """Unit Gaussian white noise drawn on the device by torch's seeded generator (large workloads,
+    where drawing 10^9 values on the host would dominate the set-up time)."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    return torch.randn(np_side ** 3, generator=g, device=device, dtype=torch.float32)

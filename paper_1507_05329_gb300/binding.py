@@ -72,7 +72,12 @@ SIGNATURES = {
     "cola_step": ([_VP, _I, _VP, _VP, _VP, _VP], _I),
     "cola_run": ([_VP, _VP, _VP, _VP, _VP, _VP, _VP, _I], _I),
     "cola_power_spectrum": ([_VP, _VP, _VP, _I], _I),
+    "cola_profile_enable": ([_VP, _I], _I),
+    "cola_profile_read": ([_VP, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong), _I], _I),
 }
+
+STAGES = ["deposit", "fwd_z_r2c", "fwd_y", "green_x", "inv_y", "inv_z_c2r", "gather_kick_drift", "x_pass",
+          "ic_elementwise", "pk_bins", "clear"]
 
 
 def load_library(path: str = LIB_PATH):
@@ -187,16 +192,35 @@ class Context:
         _check(self.lib.cola_step(self._ptr, int(i), self._particles(s), self._particles(v),
                                   self._particles(psi1), self._particles(psi2)), "cola_step")
 
+    def profile(self, on: bool = True):
+        """Start (reset) or stop CUDA-event timing of every library launch on this stream."""
+        _check(self.lib.cola_profile_enable(self._ptr, 1 if on else 0), "cola_profile_enable")
+
+    def profile_read(self) -> dict:
+        """{stage: (total ms, launches)} since the last profile(True); synchronises the stream."""
+        ms = (ctypes.c_double * len(STAGES))()
+        cnt = (ctypes.c_longlong * len(STAGES))()
+        r = self.lib.cola_profile_read(self._ptr, ms, cnt, len(STAGES))
+        if r < 0:
+            raise ColaError(-r, "cola_profile_read")
+        return {name: (ms[i], cnt[i]) for i, name in enumerate(STAGES)}
+
     def power_spectrum(self, s, nbins: int = 64):
         pk = self.torch.empty((3, nbins), dtype=self.torch.float64, device=self.device)
         _check(self.lib.cola_power_spectrum(self._ptr, self._particles(s), _ptr(pk, self.torch), int(nbins)),
                "cola_power_spectrum")
         return pk
 
-    def run(self, white_noise, nbins: int = 64, with_pk: bool = True):
+    def run(self, white_noise, nbins: int = 64, with_pk: bool = True, out: dict | None = None):
+        """A whole realisation (cola_run).  ``out`` may hold preallocated s, v, psi1, psi2, pk tensors."""
         wn = _ptr(white_noise, self.torch, (self.p.n,), self.torch.float32)
-        s, v, p1, p2 = (self.empty_particles() for _ in range(4))
-        pk = self.torch.empty((3, nbins), dtype=self.torch.float64, device=self.device) if with_pk else None
+        if out is None:
+            s, v, p1, p2 = (self.empty_particles() for _ in range(4))
+            pk = self.torch.empty((3, nbins), dtype=self.torch.float64, device=self.device) if with_pk else None
+        else:
+            s, v, p1, p2, pk = out["s"], out["v"], out["psi1"], out["psi2"], out.get("pk")
+            if with_pk:
+                _ptr(pk, self.torch, (3, nbins), self.torch.float64)
         _check(self.lib.cola_run(self._ptr, wn, self._particles(s), self._particles(v), self._particles(p1),
                                  self._particles(p2), _ptr(pk, self.torch) if with_pk else None, int(nbins)),
                "cola_run")

@@ -74,17 +74,48 @@ void bin_edges(int nmesh, int nbins, long long* e) {
   }
 }
 
+enum Stage {
+  kStDeposit = 0, kStFwdZ = 1, kStFwdY = 2, kStGreenX = 3, kStInvY = 4, kStInvZ = 5, kStGather = 6,
+  kStFwdX = 7, kStIc = 8, kStPk = 9, kStClear = 10
+};
+
+cudaEvent_t take_event(cola_ctx* c) {
+  if (!c->event_pool.empty()) {
+    cudaEvent_t e = c->event_pool.back();
+    c->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Counts the launch of one stage and, while profiling, brackets it with events on the stream.
+template <class F>
+int staged(cola_ctx* c, int stage, F&& launch) {
+  c->stage_launches[stage] += 1;
+  if (!c->prof) return launch();
+  cola_ctx::Mark m{stage, take_event(c), take_event(c)};
+  cudaEventRecord(m.a, c->stream);
+  const int st = launch();
+  cudaEventRecord(m.b, c->stream);
+  c->marks.push_back(m);
+  return st;
+}
+
+#define STAGED(stage, expr) staged(c, (stage), [&]() { return (expr); })
+
 int check_ptr(const void* p) { return (p && ((uintptr_t)p % 16 == 0)) ? COLA_OK : COLA_ERR_INVALID; }
 
 // S1 + S2 (z, y): deposit and the first two forward passes into cbuf[2].
 int deposit_and_forward_yz(cola_ctx* c, const float* s) {
   const Grid3& g = c->mesh;
   const size_t n3 = (size_t)g.n * g.n * g.n;
-  COLA_TRY(cuda_status(cudaMemsetAsync(c->rho, 0, n3 * sizeof(unsigned long long), c->stream), "memset"));
-  COLA_TRY(launch_deposit(c->pg, s, c->rho, c->flags, c->stream));
+  COLA_TRY(STAGED(kStClear, cuda_status(cudaMemsetAsync(c->rho, 0, n3 * sizeof(unsigned long long), c->stream), "memset")));
+  COLA_TRY(STAGED(kStDeposit, launch_deposit(c->pg, s, c->rho, c->flags, c->stream)));
   const float scale = (float)((double)n3 / ((double)c->pg.npart * 4398046511104.0));   // N^3 / (n 2^42)
-  COLA_TRY(launch_r2c_rows(c->mplan, g, kSrcFixedPoint, c->rho, g.n, scale, c->cbuf[2], c->stream));
-  COLA_TRY(launch_pencils(c->mplan, g, 1, -1, c->cbuf[2], c->stream));
+  COLA_TRY(STAGED(kStFwdZ, launch_r2c_rows(c->mplan, g, kSrcFixedPoint, c->rho, g.n, scale, c->cbuf[2], c->stream)));
+  COLA_TRY(STAGED(kStFwdY, launch_pencils(c->mplan, g, 1, -1, c->cbuf[2], c->stream)));
   return COLA_OK;
 }
 
@@ -93,23 +124,23 @@ int force_mesh(cola_ctx* c, const float* s, double force_scale) {
   const Grid3& g = c->mesh;
   COLA_TRY(deposit_and_forward_yz(c, s));
   float2* const outs[3] = {c->cbuf[0], c->cbuf[1], c->cbuf[2]};
-  COLA_TRY(launch_green_x(c->mplan, g, c->cbuf[2], outs, c->dtab, (float)force_scale, c->stream));
+  COLA_TRY(STAGED(kStGreenX, launch_green_x(c->mplan, g, c->cbuf[2], outs, c->dtab, (float)force_scale, c->stream)));
   for (int j = 0; j < 3; ++j) {
-    COLA_TRY(launch_pencils(c->mplan, g, 1, +1, c->cbuf[j], c->stream));
-    COLA_TRY(launch_c2r_rows(c->mplan, g, c->cbuf[j], c->stream));
+    COLA_TRY(STAGED(kStInvY, launch_pencils(c->mplan, g, 1, +1, c->cbuf[j], c->stream)));
+    COLA_TRY(STAGED(kStInvZ, launch_c2r_rows(c->mplan, g, c->cbuf[j], c->stream)));
   }
   return COLA_OK;
 }
 
 int inverse3d(cola_ctx* c, const Grid3& g, const FftPlan& p, float2* b) {
-  COLA_TRY(launch_pencils(p, g, 0, +1, b, c->stream));
-  COLA_TRY(launch_pencils(p, g, 1, +1, b, c->stream));
-  return launch_c2r_rows(p, g, b, c->stream);
+  COLA_TRY(STAGED(kStFwdX, launch_pencils(p, g, 0, +1, b, c->stream)));
+  COLA_TRY(STAGED(kStInvY, launch_pencils(p, g, 1, +1, b, c->stream)));
+  return STAGED(kStInvZ, launch_c2r_rows(p, g, b, c->stream));
 }
 
 int forward3d_yx(cola_ctx* c, const Grid3& g, const FftPlan& p, float2* b) {
-  COLA_TRY(launch_pencils(p, g, 1, -1, b, c->stream));
-  return launch_pencils(p, g, 0, -1, b, c->stream);
+  COLA_TRY(STAGED(kStFwdY, launch_pencils(p, g, 1, -1, b, c->stream)));
+  return STAGED(kStFwdX, launch_pencils(p, g, 0, -1, b, c->stream));
 }
 
 }  // namespace
@@ -148,6 +179,11 @@ extern "C" int cola_step_scalars(const cola_params* params, int i, double* out, 
 extern "C" void cola_destroy(cola_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
+  for (auto& m : c->marks) {
+    cudaEventDestroy(m.a);
+    cudaEventDestroy(m.b);
+  }
+  for (cudaEvent_t e : c->event_pool) cudaEventDestroy(e);
   if (c->edges_host) cudaFreeHost(c->edges_host);
   fft_plan_free(&c->mplan);
   fft_plan_free(&c->lplan);
@@ -275,34 +311,34 @@ extern "C" int cola_ic_2lpt(cola_ctx* c, const float* wn, float* s, float* v, fl
   const long long n = c->pg.npart;
   const float r = (float)c->p.nmesh / (float)c->p.np;   // lattice spacings -> mesh cells
   // white noise -> W(k) -> delta_L(k) / np^3
-  COLA_TRY(launch_r2c_rows(P, g, kSrcFloat, wn, g.n, 1.0f, B[0], c->stream));
+  COLA_TRY(STAGED(kStFwdZ, launch_r2c_rows(P, g, kSrcFloat, wn, g.n, 1.0f, B[0], c->stream)));
   COLA_TRY(forward3d_yx(c, g, P, B[0]));
-  COLA_TRY(launch_ic_amplitude(g, B[0], c->amp_m2, c->stream));
+  COLA_TRY(STAGED(kStIc, launch_ic_amplitude(g, B[0], c->amp_m2, c->stream)));
   // Psi1 = i k delta_L / k^2
   for (int j = 0; j < 3; ++j) {
-    COLA_TRY(launch_ic_multiply(g, B[0], B[7], kIcPsi1, j, 0, 1.0f, c->stream));
+    COLA_TRY(STAGED(kStIc, launch_ic_multiply(g, B[0], B[7], kIcPsi1, j, 0, 1.0f, c->stream)));
     COLA_TRY(inverse3d(c, g, P, B[7]));
-    COLA_TRY(launch_ic_to_particles(g, B[7], r, psi1 + j * n, c->stream));
+    COLA_TRY(STAGED(kStIc, launch_ic_to_particles(g, B[7], r, psi1 + j * n, c->stream)));
   }
   // phi1_ij = k_i k_j delta_L / k^2 in real space, then the second-order source
   const int pairs[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
   for (int h = 0; h < 6; ++h) {
-    COLA_TRY(launch_ic_multiply(g, B[0], B[1 + h], kIcHess, pairs[h][0], pairs[h][1], 1.0f, c->stream));
+    COLA_TRY(STAGED(kStIc, launch_ic_multiply(g, B[0], B[1 + h], kIcHess, pairs[h][0], pairs[h][1], 1.0f, c->stream)));
     COLA_TRY(inverse3d(c, g, P, B[1 + h]));
   }
   float2* const hs[6] = {B[1], B[2], B[3], B[4], B[5], B[6]};
-  COLA_TRY(launch_ic_source(g, hs, B[7], c->stream));
-  COLA_TRY(launch_r2c_rows(P, g, kSrcFloat, B[7], 2LL * g.pc, 1.0f, B[7], c->stream));
+  COLA_TRY(STAGED(kStIc, launch_ic_source(g, hs, B[7], c->stream)));
+  COLA_TRY(STAGED(kStFwdZ, launch_r2c_rows(P, g, kSrcFloat, B[7], 2LL * g.pc, 1.0f, B[7], c->stream)));
   COLA_TRY(forward3d_yx(c, g, P, B[7]));
   // Psi2 = -i k S(k) / k^2
   const float inv_n3 = (float)(1.0 / ((double)g.n * g.n * g.n));
   for (int j = 0; j < 3; ++j) {
-    COLA_TRY(launch_ic_multiply(g, B[7], B[1], kIcPsi2, j, 0, inv_n3, c->stream));
+    COLA_TRY(STAGED(kStIc, launch_ic_multiply(g, B[7], B[1], kIcPsi2, j, 0, inv_n3, c->stream)));
     COLA_TRY(inverse3d(c, g, P, B[1]));
-    COLA_TRY(launch_ic_to_particles(g, B[1], r, psi2 + j * n, c->stream));
+    COLA_TRY(STAGED(kStIc, launch_ic_to_particles(g, B[1], r, psi2 + j * n, c->stream)));
   }
   const StepScalars& s0 = c->steps[0];
-  return launch_ic_positions(n, psi1, psi2, (float)s0.d1, (float)s0.d2, s, v, c->stream);
+  return STAGED(kStIc, launch_ic_positions(n, psi1, psi2, (float)s0.d1, (float)s0.d2, s, v, c->stream));
 }
 
 extern "C" int cola_deposit(cola_ctx* c, const float* s, unsigned long long* rho) {
@@ -319,7 +355,7 @@ extern "C" int cola_density_spectrum(cola_ctx* c, const float* s, float* delta_k
   COLA_TRY(check_ptr(s));
   COLA_TRY(check_ptr(delta_k));
   COLA_TRY(deposit_and_forward_yz(c, s));
-  COLA_TRY(launch_pencils(c->mplan, c->mesh, 0, -1, c->cbuf[2], c->stream));
+  COLA_TRY(STAGED(kStFwdX, launch_pencils(c->mplan, c->mesh, 0, -1, c->cbuf[2], c->stream)));
   return launch_dense_spectrum(c->mesh, c->cbuf[2], delta_k, c->stream);
 }
 
@@ -330,8 +366,8 @@ extern "C" int cola_pm_force(cola_ctx* c, const float* s, double a, float* force
   COLA_TRY(force_mesh(c, s, 1.5 * c->p.omega_m / a));
   const float* f[3] = {reinterpret_cast<float*>(c->cbuf[0]), reinterpret_cast<float*>(c->cbuf[1]),
                        reinterpret_cast<float*>(c->cbuf[2])};
-  return launch_gather(c->pg, f, 2LL * c->mesh.pc, s, force, nullptr, nullptr, nullptr, nullptr, nullptr,
-                       c->flags, c->stream);
+  return STAGED(kStGather, launch_gather(c->pg, f, 2LL * c->mesh.pc, s, force, nullptr, nullptr, nullptr, nullptr,
+                                         nullptr, c->flags, c->stream));
 }
 
 extern "C" int cola_step(cola_ctx* c, int i, float* s, float* v, const float* psi1, const float* psi2) {
@@ -343,7 +379,8 @@ extern "C" int cola_step(cola_ctx* c, int i, float* s, float* v, const float* ps
   const KickDrift kd{(float)ss.kick, (float)ss.drift, (float)ss.dd1, (float)ss.dd2, (float)ss.c1, (float)ss.c2};
   const float* f[3] = {reinterpret_cast<float*>(c->cbuf[0]), reinterpret_cast<float*>(c->cbuf[1]),
                        reinterpret_cast<float*>(c->cbuf[2])};
-  return launch_gather(c->pg, f, 2LL * c->mesh.pc, nullptr, nullptr, s, v, psi1, psi2, &kd, c->flags, c->stream);
+  return STAGED(kStGather, launch_gather(c->pg, f, 2LL * c->mesh.pc, nullptr, nullptr, s, v, psi1, psi2, &kd,
+                                         c->flags, c->stream));
 }
 
 extern "C" int cola_power_spectrum(cola_ctx* c, const float* s, double* pk, int nbins) {
@@ -359,13 +396,13 @@ extern "C" int cola_power_spectrum(cola_ctx* c, const float* s, double* pk, int 
     c->edges_nbins = nbins;
   }
   COLA_TRY(deposit_and_forward_yz(c, s));
-  COLA_TRY(launch_pencils(c->mplan, c->mesh, 0, -1, c->cbuf[2], c->stream));
+  COLA_TRY(STAGED(kStFwdX, launch_pencils(c->mplan, c->mesh, 0, -1, c->cbuf[2], c->stream)));
   const double nn = c->mesh.n;
   const double pscale = std::pow(c->p.box, 3) / (nn * nn * nn * nn * nn * nn);
   const double kfund = 2.0 * M_PI / c->p.box;
-  COLA_TRY(launch_pk_bins(c->mesh, c->cbuf[2], c->edges, nbins, pscale, kfund, c->pk_partials, c->pk_blocks,
-                          c->stream));
-  return launch_pk_finish(c->pk_partials, c->pk_blocks, nbins, pk, c->stream);
+  COLA_TRY(STAGED(kStPk, launch_pk_bins(c->mesh, c->cbuf[2], c->edges, nbins, pscale, kfund, c->pk_partials,
+                                        c->pk_blocks, c->stream)));
+  return STAGED(kStPk, launch_pk_finish(c->pk_partials, c->pk_blocks, nbins, pk, c->stream));
 }
 
 extern "C" int cola_run(cola_ctx* c, const float* wn, float* s, float* v, float* psi1, float* psi2, double* pk,
@@ -375,4 +412,40 @@ extern "C" int cola_run(cola_ctx* c, const float* wn, float* s, float* v, float*
   for (int i = 1; i <= c->p.nstep; ++i) COLA_TRY(cola_step(c, i, s, v, psi1, psi2));
   if (pk) COLA_TRY(cola_power_spectrum(c, s, pk, nbins));
   return COLA_OK;
+}
+
+extern "C" int cola_profile_enable(cola_ctx* c, int on) {
+  if (!c) return COLA_ERR_INVALID;
+  if (on) {
+    COLA_TRY(cuda_status(cudaStreamSynchronize(c->stream), "profile sync"));
+    for (auto& m : c->marks) {
+      c->event_pool.push_back(m.a);
+      c->event_pool.push_back(m.b);
+    }
+    c->marks.clear();
+    for (int i = 0; i < COLA_NUM_STAGES; ++i) {
+      c->stage_ms[i] = 0.0;
+      c->stage_launches[i] = 0;
+    }
+  }
+  c->prof = on != 0;
+  return COLA_OK;
+}
+
+extern "C" int cola_profile_read(cola_ctx* c, double* ms, long long* launches, int nstages) {
+  if (!c || nstages < 0) return -COLA_ERR_INVALID;
+  if (cuda_status(cudaStreamSynchronize(c->stream), "profile read") != COLA_OK) return -COLA_ERR_CUDA;
+  for (auto& m : c->marks) {
+    float t = 0.0f;
+    cudaEventElapsedTime(&t, m.a, m.b);
+    c->stage_ms[m.stage] += t;
+    c->event_pool.push_back(m.a);
+    c->event_pool.push_back(m.b);
+  }
+  c->marks.clear();
+  for (int i = 0; i < nstages && i < COLA_NUM_STAGES; ++i) {
+    if (ms) ms[i] = c->stage_ms[i];
+    if (launches) launches[i] = c->stage_launches[i];
+  }
+  return COLA_NUM_STAGES;
 }

@@ -148,4 +148,11 @@ struct cola_ctx {
   double* pk_partials = nullptr;
   int pk_blocks = 0;
   int* flags = nullptr;                   // sticky device error flags
+  // measurement support
+  bool prof = false;
+  double stage_ms[COLA_NUM_STAGES] = {};
+  long long stage_launches[COLA_NUM_STAGES] = {};
+  struct Mark { int stage; cudaEvent_t a, b; };
+  std::vector<Mark> marks;
+  std::vector<cudaEvent_t> event_pool;
 };
