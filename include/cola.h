@@ -145,6 +145,30 @@ int cola_power_spectrum(cola_ctx* ctx, const float* s, double* pk, int nbins);
 int cola_profile_enable(cola_ctx* ctx, int on);
 int cola_profile_read(cola_ctx* ctx, double* ms, long long* launches, int nstages);
 
+/* Allocation-free power spectrum (this entry point has no counterpart in the paper).
+ *
+ * For callers that cannot allocate device memory: code that runs inside a CUDA-graph capture and
+ * must replay without a memory pool, plug-ins whose host framework owns the whole device heap,
+ * and real-time loops that forbid allocator calls (cudaMalloc also synchronises the device).
+ * It computes what cola_power_spectrum computes, without a context and without any allocation:
+ * its scratch (density mesh, spectrum, partial sums, twiddles, bin edges) is one static device
+ * array of COLA_NOALLOC_SCRATCH_BYTES that every GPU loading this library holds until exit.
+ *   params : only np, nmesh and box are used; nmesh <= COLA_NOALLOC_MAX_MESH, np <= COLA_NOALLOC_MAX_NP
+ *            (fewer than 2^22 particles: the fixed-point mesh cannot overflow), same size rules as
+ *            cola_create.  Larger sizes return COLA_ERR_INVALID before anything is launched.
+ *   s      : device float32 [3][np^3] displacements (mesh cells), 16-byte aligned.
+ *   pk     : device double [3][nbins], as for cola_power_spectrum; 1 <= nbins <= 128.
+ *   stream : cudaStream_t to enqueue on (NULL = legacy default stream).
+ * Asynchronous: results are ready when the stream reaches them.  The first call on each device
+ * resolves the array's device address (cudaGetSymbolAddress) and raises the FFT kernels' shared
+ * memory limit; make that first call before any stream capture.  Every call shares the array:
+ * calls that overlap on the GPU (other streams or threads) race and give wrong results. */
+#define COLA_NOALLOC_MAX_MESH 64
+#define COLA_NOALLOC_MAX_NP 128
+#define COLA_NOALLOC_SCRATCH_BYTES 3670016
+int cola_power_spectrum_noalloc(const cola_params* params, const float* s, double* pk, int nbins,
+                                void* stream);
+
 #ifdef __cplusplus
 }
 #endif

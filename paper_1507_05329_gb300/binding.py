@@ -74,6 +74,7 @@ SIGNATURES = {
     "cola_power_spectrum": ([_VP, _VP, _VP, _I], _I),
     "cola_profile_enable": ([_VP, _I], _I),
     "cola_profile_read": ([_VP, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong), _I], _I),
+    "cola_power_spectrum_noalloc": ([ctypes.POINTER(CParams), _VP, _VP, _I, _VP], _I),
 }
 
 STAGES = ["deposit", "fwd_z_r2c", "fwd_y", "green_x", "inv_y", "inv_z_c2r", "gather_kick_drift", "x_pass",
@@ -108,6 +109,20 @@ def step_scalars(p: Params, i: int) -> list[float]:
     cp = p.to_c()
     _check(lib.cola_step_scalars(ctypes.byref(cp), i, out, 12), "cola_step_scalars")
     return list(out)
+
+
+def power_spectrum_noalloc(p: Params, s, nbins: int = 64, stream=None):
+    """P(k) of displacements s through the allocation-free entry point (no context; meshes up to
+    64^3).  Returns a new [3, nbins] float64 tensor; the library itself allocates nothing."""
+    import torch
+    lib = load_library()
+    st = stream if stream is not None else torch.cuda.current_stream()
+    pk = torch.empty((3, nbins), dtype=torch.float64, device=s.device)
+    cp = p.to_c()
+    _check(lib.cola_power_spectrum_noalloc(ctypes.byref(cp), _ptr(s, torch, (3, p.n), torch.float32),
+                                           _ptr(pk, torch), int(nbins), ctypes.c_void_p(st.cuda_stream)),
+           "cola_power_spectrum_noalloc")
+    return pk
 
 
 def _ptr(t, torch, shape=None, dtype=None):

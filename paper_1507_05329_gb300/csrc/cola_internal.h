@@ -58,6 +58,7 @@ struct FftPlan {
 bool fft_factor(int n, std::vector<int>* radices);
 int fft_plan_init(FftPlan* plan, int n);   // allocates the twiddle table; returns cola_status
 void fft_plan_free(FftPlan* plan);
+void fft_set_smem_limits();                // raise the dynamic shared-memory limit of the FFT kernels
 
 // Geometry of a 3D field of side n in the in-place real-to-complex layout:
 // complex rows of pc = (n/2+1 rounded up to even) entries, real rows of 2*pc floats.

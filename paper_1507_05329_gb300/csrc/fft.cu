@@ -430,6 +430,16 @@ int fft_plan_init(FftPlan* plan, int n) {
   return COLA_OK;
 }
 
+void fft_set_smem_limits() {
+  const int mx = 227 * 1024;
+  cudaFuncSetAttribute(k_r2c_rows<kSrcFixedPoint>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_r2c_rows<kSrcFloat>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_c2r_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_pencils<-1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_pencils<+1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_green_x, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+}
+
 void fft_plan_free(FftPlan* plan) {
   if (plan->tw) cudaFree(plan->tw);
   plan->tw = nullptr;
