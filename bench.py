@@ -174,7 +174,7 @@ def run_reference(args):
 # ---- our arm -------------------------------------------------------------------------------------
 def source_digest() -> str:
     h = hashlib.sha256()
-    for f in ("fft.cu", "particles.cu", "cola_abi.cu", "cola_internal.h"):
+    for f in ("fft.cu", "particles.cu", "binning.cu", "cola_abi.cu", "cola_internal.h"):
         with open(os.path.join(ROOT, "paper_1507_05329_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -276,6 +276,9 @@ def run_ours(args):
             per_stage[k] = {"avg_ms": round(a, 4), "launches": prof[k][1],
                             "GBps": round(sb[k] / (a / 1e3) / 1e9, 1), "frac": round(sb[k] / (a / 1e3) / 1e9 / peak, 3)}
     launches = sum(v[1] for k, v in prof.items() if k != "clear")
+    if prof.get("bin", (0, 0))[1]:
+        per_stage["bin"] = {"avg_ms": round(prof["bin"][0] / prof["bin"][1], 4), "launches": prof["bin"][1],
+                            "note": "particle binning by mesh tiles (implementation overhead, not algorithmic bytes)"}
     pm_ms = sum(prof[k][0] for k in sb) / args.steps
 
     # end to end through the public API with host buffers (pinned), copies inside the timed region

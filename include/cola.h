@@ -135,13 +135,14 @@ int cola_power_spectrum(cola_ctx* ctx, const float* s, double* pk, int nbins);
  * Stages: 0 deposit, 1 forward z (R2C), 2 forward y, 3 x + Green + gradient + inverse x,
  * 4 inverse y, 5 inverse z (C2R), 6 gather + kick + drift (or force gather), 7 x passes outside
  * the fused stage 3 (P(k), density spectrum, 2LPT), 8 2LPT element-wise kernels, 9 P(k) binning,
- * 10 mesh clearing (memset).  Stages 1, 2, 4 and 5 also count the 2LPT transforms.
+ * 10 mesh clearing (memset, direct deposit only), 11 spatial binning of the particles (count, scan,
+ * scatter).  Stages 1, 2, 4 and 5 also count the 2LPT transforms.
  * cola_profile_enable(ctx, 1) resets the totals and brackets every later launch with CUDA events
  * on the context's stream; 0 stops timing (launches are always counted).  cola_profile_read
  * synchronises the stream and writes per-stage total milliseconds and launch counts for the first
- * nstages stages (either pointer may be NULL).  Returns the number of stages (11), or minus a
+ * nstages stages (either pointer may be NULL).  Returns the number of stages (12), or minus a
  * cola_status on failure. */
-#define COLA_NUM_STAGES 11
+#define COLA_NUM_STAGES 12
 int cola_profile_enable(cola_ctx* ctx, int on);
 int cola_profile_read(cola_ctx* ctx, double* ms, long long* launches, int nstages);
 

@@ -78,7 +78,7 @@ SIGNATURES = {
 }
 
 STAGES = ["deposit", "fwd_z_r2c", "fwd_y", "green_x", "inv_y", "inv_z_c2r", "gather_kick_drift", "x_pass",
-          "ic_elementwise", "pk_bins", "clear"]
+          "ic_elementwise", "pk_bins", "clear", "bin"]
 
 
 def load_library(path: str = LIB_PATH):

@@ -1,0 +1,506 @@
+// Spatial binning of particles by mesh column tiles, and the tile-wise CIC deposit and gather.
+//
+// The particle arrays stay in Lagrangian order (particle id = lattice index).  At late times the
+// particles of one lattice plane are spread over tens of mesh planes (§2.3 mesh; displacements of
+// ~8 cells rms at a = 1 for the 0.78 Mpc/h cells of the 1536^3 mesh), so visiting them in lattice
+// order touches far more mesh than the L2 holds.  Each step therefore
+//   1. counts particles per tile of T x T x TZ mesh cells (T = 8 across, TZ = 32 along z) from the
+//      fixed-point base cell (the same integer cell as the deposit), with warp-aggregated atomics;
+//   2. scans the counts into offsets;
+//   3. scatters packed lattice coordinates into their tile's list.  A particle whose base cell
+//      lies on an upper face of its tile also goes, as a "spill" entry, to the neighbouring tiles
+//      its cloud reaches (at most seven);
+//   4. deposits tile by tile: one CTA sums the 8 fixed-point weights of its primary and spill
+//      particles that fall inside the tile in shared memory (64-bit integers, exact) and writes
+//      the whole tile once with plain stores: no clearing pass and no global atomics on the mesh;
+//   5. gathers the force and applies the kick and drift tile by tile (primary entries only): the
+//      CTA first copies the tile's force values with a one-cell halo ((T+1)^2 (TZ+1) x 3 floats,
+//      32 KB) into shared memory with coalesced loads, then interpolates from shared memory.  The
+//      tile index runs fastest along z, so neighbouring tiles (which share halos) run together.
+// The order of particles inside a tile's list depends on atomic timing, but neither result does:
+// integer sums are order independent and every particle's gather is computed on its own.
+#include "cola_internal.h"
+
+#include <cstdio>
+
+namespace cola {
+namespace {
+
+constexpr int kFracBits = 20;
+constexpr long long kFracOne = 1LL << kFracBits;
+constexpr int kWeightOne = 1 << 14;
+constexpr int kThreads = 256;
+
+int check_launch(const char* what) {
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    std::fprintf(stderr, "cola: launch of %s failed: %s\n", what, cudaGetErrorString(e));
+    return COLA_ERR_CUDA;
+  }
+  return COLA_OK;
+}
+
+__device__ __forceinline__ long long fixed_coord(int q, float s, long long r_fixed, long long modulus) {
+  long long g = (long long)q * r_fixed + __float2ll_rn(s * (float)kFracOne);
+  if (g < 0) g += modulus;
+  else if (g >= modulus) g -= modulus;
+  if ((unsigned long long)g >= (unsigned long long)modulus) {
+    g %= modulus;
+    if (g < 0) g += modulus;
+  }
+  return g;
+}
+
+// Bin entries hold the lattice coordinates packed as qx << 20 | qy << 10 | qz (np <= 1024).
+__device__ __forceinline__ unsigned pack_q(int qx, int qy, int qz) {
+  return ((unsigned)qx << 20) | ((unsigned)qy << 10) | (unsigned)qz;
+}
+__device__ __forceinline__ void unpack_q(unsigned e, int np, int* q, long long* id) {
+  q[0] = (int)(e >> 20);
+  q[1] = (int)((e >> 10) & 1023u);
+  q[2] = (int)(e & 1023u);
+  *id = ((long long)q[0] * np + q[1]) * np + q[2];
+}
+
+// Exact 64-bit shared-memory add from two native 32-bit atomics (low word with carry out).
+__device__ __forceinline__ void smem_add64(unsigned long long* p, unsigned long long w) {
+  unsigned* h = reinterpret_cast<unsigned*>(p);
+  const unsigned lo = (unsigned)w, hi = (unsigned)(w >> 32);
+  const unsigned old = atomicAdd(h, lo);
+  const unsigned carry = (old + lo) < old ? 1u : 0u;
+  if (hi + carry) atomicAdd(h + 1, hi + carry);
+}
+
+// warp-aggregated increment of counter[key] for the lanes whose key >= 0; returns the lane's slot
+// (old value + rank among equal keys) when want_slot.
+__device__ __forceinline__ unsigned agg_inc(unsigned* counter, int key, bool want_slot) {
+  const unsigned active = __activemask();
+  const unsigned grp = __match_any_sync(active, key);
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(grp) - 1;
+  unsigned base = 0;
+  if (key >= 0 && lane == leader) base = atomicAdd(counter + key, (unsigned)__popc(grp));
+  if (!want_slot) return 0;
+  base = __shfl_sync(grp, base, leader);
+  return base + __popc(grp & ((1u << lane) - 1u));
+}
+
+// Bin keys of one particle: primary tile and up to seven spill tiles (-1 = none).  Tile index
+// (bx * nt + by) * nz + bz runs fastest along z.
+__device__ __forceinline__ void tile_keys(const BinGeom& b, int cx, int cy, int cz, int* k) {
+  const int bx = cx >> b.lt, by = cy >> b.lt, bz = cz >> b.lz;
+  const int m = (1 << b.lt) - 1, mz = (1 << b.lz) - 1;
+  // with a single tile along an axis the cloud wraps inside the tile itself: no spill there
+  const bool sx = b.nt > 1 && (cx & m) == m, sy = b.nt > 1 && (cy & m) == m, sz = b.nz > 1 && (cz & mz) == mz;
+  const int bxs[2] = {bx, bx + 1 == b.nt ? 0 : bx + 1};
+  const int bys[2] = {by, by + 1 == b.nt ? 0 : by + 1};
+  const int bzs[2] = {bz, bz + 1 == b.nz ? 0 : bz + 1};
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const int dx = c >> 2, dy = (c >> 1) & 1, dz = c & 1;
+    const bool ok = (!dx || sx) && (!dy || sy) && (!dz || sz);
+    k[c] = ok ? (bxs[dx] * b.nt + bys[dy]) * b.nz + bzs[dz] : -1;
+  }
+}
+
+template <bool SCATTER>
+__global__ void __launch_bounds__(kThreads) k_bin(ParticleGeom pg, BinGeom b, const float* __restrict__ s,
+                                                  unsigned* cnt_p, unsigned* cnt_s, unsigned* ent_p, unsigned* ent_s) {
+  const long long n = pg.npart;
+  const long long modulus = (long long)pg.n << kFracBits;
+  const int np = pg.np;
+  const long long nrows = (long long)np * np;
+  for (long long row = blockIdx.x; row < nrows; row += gridDim.x) {
+    const int qx = (int)(row / np), qy = (int)(row - (long long)qx * np);
+    // whole warps walk the row together so that the warp-aggregated atomics see full warps
+    for (int qz0 = 0; qz0 < np; qz0 += blockDim.x) {
+      const int qz = qz0 + threadIdx.x;
+      const bool live = qz < np;
+      const long long id = row * np + qz;
+      int k[8] = {-1, -1, -1, -1, -1, -1, -1, -1};
+      if (live) {
+        const int cx = (int)(fixed_coord(qx, __ldg(s + id), pg.r_fixed, modulus) >> kFracBits);
+        const int cy = (int)(fixed_coord(qy, __ldg(s + n + id), pg.r_fixed, modulus) >> kFracBits);
+        const int cz = (int)(fixed_coord(qz, __ldg(s + 2 * n + id), pg.r_fixed, modulus) >> kFracBits);
+        tile_keys(b, cx, cy, cz, k);
+      }
+      const unsigned packed = pack_q(qx, qy, qz);
+      if (__any_sync(__activemask(), live)) {
+        // primary keys are shared by runs of lanes: one aggregated atomic per run
+        const unsigned slot = agg_inc(cnt_p, k[0], SCATTER);
+        if (SCATTER && k[0] >= 0) ent_p[slot] = packed;
+      }
+      // spill keys are sparse: one atomic per entry
+#pragma unroll
+      for (int e = 1; e < 8; ++e) {
+        if (k[e] >= 0) {
+          const unsigned sl = atomicAdd(cnt_s + k[e], 1u);
+          if (SCATTER) ent_s[sl] = packed;
+        }
+      }
+    }
+  }
+}
+
+// Exclusive scan of the two per-tile count arrays into offsets (length m+1) and scatter cursors,
+// in three coalesced phases: per-segment sums, a scan of the segment sums, per-segment scans.
+constexpr int kScanThreads = 512;
+constexpr int kScanSeg = kScanThreads * 8;   // counts per segment
+
+__device__ __forceinline__ unsigned block_excl_scan(unsigned v, unsigned* total) {
+  __shared__ unsigned wsum[kScanThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned incl = v;
+  for (int d = 1; d < 32; d <<= 1) {
+    const unsigned o = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= d) incl += o;
+  }
+  if (lane == 31) wsum[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    unsigned w = lane < kScanThreads / 32 ? wsum[lane] : 0;
+    for (int d = 1; d < 32; d <<= 1) {
+      const unsigned o = __shfl_up_sync(0xffffffffu, w, d);
+      if (lane >= d) w += o;
+    }
+    if (lane < kScanThreads / 32) wsum[lane] = w;
+  }
+  __syncthreads();
+  const unsigned before = warp ? wsum[warp - 1] : 0;
+  *total = wsum[kScanThreads / 32 - 1];
+  __syncthreads();
+  return before + incl - v;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_sums(const unsigned* __restrict__ cnt_p,
+                                                           const unsigned* __restrict__ cnt_s, int m,
+                                                           unsigned* seg_sums) {
+  const int list = blockIdx.y;
+  const unsigned* cnt = list ? cnt_s : cnt_p;
+  const int base = blockIdx.x * kScanSeg;
+  unsigned v = 0;
+  for (int i = threadIdx.x; i < kScanSeg; i += kScanThreads)
+    if (base + i < m) v += cnt[base + i];
+  unsigned tot;
+  block_excl_scan(v, &tot);
+  if (threadIdx.x == 0) seg_sums[list * gridDim.x + blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_segs(unsigned* seg_sums, int nseg) {
+  const int list = blockIdx.x;
+  unsigned* ss = seg_sums + list * nseg;
+  unsigned carry = 0;
+  for (int b = 0; b < nseg; b += kScanThreads) {
+    const unsigned v = b + (int)threadIdx.x < nseg ? ss[b + threadIdx.x] : 0;
+    unsigned tot;
+    const unsigned ex = block_excl_scan(v, &tot);
+    if (b + (int)threadIdx.x < nseg) ss[b + threadIdx.x] = carry + ex;
+    carry += tot;
+  }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(const unsigned* __restrict__ cnt_p,
+                                                            const unsigned* __restrict__ cnt_s, int m,
+                                                            const unsigned* __restrict__ seg_sums, unsigned* off_p,
+                                                            unsigned* off_s, unsigned* cur_p, unsigned* cur_s) {
+  const int list = blockIdx.y;
+  const unsigned* cnt = list ? cnt_s : cnt_p;
+  unsigned* off = list ? off_s : off_p;
+  unsigned* cur = list ? cur_s : cur_p;
+  const int base = blockIdx.x * kScanSeg;
+  // each thread scans 8 consecutive counts; the thread totals are scanned across the block
+  unsigned c[8], v = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int i = base + threadIdx.x * 8 + k;
+    c[k] = i < m ? cnt[i] : 0;
+    v += c[k];
+  }
+  unsigned tot;
+  unsigned run = seg_sums[list * gridDim.x + blockIdx.x] + block_excl_scan(v, &tot);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int i = base + threadIdx.x * 8 + k;
+    if (i < m) {
+      off[i] = run;
+      cur[i] = run;
+    }
+    run += c[k];
+    if (i == m - 1) off[m] = run;
+  }
+}
+
+// Tile-wise deposit: shared accumulator [T][T][TZ] of 64-bit fixed-point sums.
+__global__ void __launch_bounds__(kThreads) k_deposit_tiles(ParticleGeom pg, BinGeom b, const float* __restrict__ s,
+                                                           const unsigned* __restrict__ off_p,
+                                                           const unsigned* __restrict__ ent_p,
+                                                           const unsigned* __restrict__ off_s,
+                                                           const unsigned* __restrict__ ent_s,
+                                                           unsigned long long* rho) {
+  extern __shared__ unsigned long long acc[];
+  const int nm = pg.n, T = 1 << b.lt, TZ = 1 << b.lz;
+  const int tile = blockIdx.x;
+  const int bz = tile % b.nz, bxy = tile / b.nz;
+  const int bx = bxy / b.nt, by = bxy - bx * b.nt;
+  const int x0 = bx << b.lt, y0 = by << b.lt, z0 = bz << b.lz;
+  const int cells = (T * T) << b.lz;
+  for (int i = threadIdx.x; i < cells; i += blockDim.x) acc[i] = 0ULL;
+  __syncthreads();
+  const long long n = pg.npart;
+  const long long modulus = (long long)nm << kFracBits;
+  for (int list = 0; list < 2; ++list) {
+    const unsigned* off = list ? off_s : off_p;
+    const unsigned* ent = list ? ent_s : ent_p;
+    const unsigned e0 = off[tile], e1 = off[tile + 1];
+    for (unsigned e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+      int q[3];
+      long long id;
+      unpack_q(ent[e], pg.np, q, &id);
+      int c[3];
+      unsigned long long w1[3], w0[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const long long g = fixed_coord(q[a], __ldg(s + a * n + id), pg.r_fixed, modulus);
+        c[a] = (int)(g >> kFracBits);
+        w1[a] = (unsigned long long)((g >> (kFracBits - 14)) & (kWeightOne - 1));
+        w0[a] = kWeightOne - w1[a];
+      }
+      int lz[2];
+#pragma unroll
+      for (int dz = 0; dz < 2; ++dz) {
+        int iz = c[2] + dz;
+        if (iz == nm) iz = 0;
+        lz[dz] = iz - z0;
+      }
+#pragma unroll
+      for (int dx = 0; dx < 2; ++dx) {
+        int ix = c[0] + dx;
+        if (ix == nm) ix = 0;
+        const int lx = ix - x0;
+        if (lx < 0 || lx >= T) continue;
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy) {
+          int iy = c[1] + dy;
+          if (iy == nm) iy = 0;
+          const int ly = iy - y0;
+          if (ly < 0 || ly >= T) continue;
+          const unsigned long long wxy = (dx ? w1[0] : w0[0]) * (dy ? w1[1] : w0[1]);
+          unsigned long long* col = acc + ((lx * T + ly) << b.lz);
+#pragma unroll
+          for (int dz = 0; dz < 2; ++dz) {
+            const unsigned long long w = wxy * (dz ? w1[2] : w0[2]);
+            if (w && lz[dz] >= 0 && lz[dz] < TZ) smem_add64(col + lz[dz], w);
+          }
+        }
+      }
+    }
+  }
+  __syncthreads();
+  // the tile owns its cells: plain, coalesced stores of T*T column segments of TZ cells
+  for (int i = threadIdx.x; i < cells; i += blockDim.x) {
+    const int col = i >> b.lz, z = i & (TZ - 1);
+    const int lx = col >> b.lt, ly = col & (T - 1);
+    rho[((long long)(x0 + lx) * nm + (y0 + ly)) * nm + z0 + z] = acc[i];
+  }
+}
+
+// Tile-wise gather (+ kick and drift) over the primary entries of each tile, from a shared copy
+// of the tile's force values with a one-cell halo on the upper side of every axis.
+template <bool KICK>
+__global__ void __launch_bounds__(kThreads) k_gather_tiles(ParticleGeom pg, BinGeom b, int gz,
+                                                          const unsigned* __restrict__ off_p,
+                                                          const unsigned* __restrict__ ent_p,
+                                                          const float* __restrict__ f0, const float* __restrict__ f1,
+                                                          const float* __restrict__ f2, long long rs,
+                                                          const float* __restrict__ s_in, float* __restrict__ force_out,
+                                                          float* s, float* v, const float* __restrict__ psi1,
+                                                          const float* __restrict__ psi2, KickDrift kd, int* flags) {
+  // one CTA: gz consecutive tiles along z (their entries are contiguous), i.e. T x T x (gz TZ) cells.
+  // Shared copy: 3 components x (T+1)^2 rows of hz = gz TZ + 1 floats, rows padded to hp (16 B).
+  extern __shared__ __align__(16) float fsm[];
+  const int nm = pg.n, T = 1 << b.lt;
+  const int tile = blockIdx.x * gz;
+  const int bz = tile % b.nz, bxy = tile / b.nz;
+  const int bx = bxy / b.nt, by = bxy - bx * b.nt;
+  const int x0 = bx << b.lt, y0 = by << b.lt, z0 = bz << b.lz;
+  const int hx = T + 1, zl = gz << b.lz, hz = zl + 1, hp = (hz + 3) & ~3;
+  const int rows = 3 * hx * hx;
+  const unsigned e0 = off_p[tile], e1 = off_p[tile + gz];
+  if (e0 == e1) return;                          // empty (uniform across the block)
+  {
+    // asynchronous copies: zl/4 chunks of 16 bytes (rows start 16-byte aligned: z0 is a multiple of
+    // TZ and real rows hold 2 pc floats, pc even) plus the 4-byte halo cell, all in flight at once
+    const int chunks = (zl >> 2) + 1;
+    for (int op = threadIdx.x; op < rows * chunks; op += blockDim.x) {
+      const int r = op / chunks, ch = op - r * chunks;
+      const int comp = r / (hx * hx), col = r - comp * hx * hx;
+      const int lx = col / hx, ly = col - lx * hx;
+      int gx = x0 + lx, gy = y0 + ly;
+      if (gx >= nm) gx -= nm;
+      if (gy >= nm) gy -= nm;
+      const float* f = comp == 0 ? f0 : (comp == 1 ? f1 : f2);
+      const float* row = f + ((long long)gx * nm + gy) * rs;
+      float* dst = fsm + r * hp;
+      if (ch < (zl >> 2)) {
+        const unsigned sa = (unsigned)__cvta_generic_to_shared(dst + 4 * ch);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(row + z0 + 4 * ch) : "memory");
+      } else {
+        const int gzz = z0 + zl == nm ? 0 : z0 + zl;   // periodic halo cell
+        const unsigned sa = (unsigned)__cvta_generic_to_shared(dst + zl);
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(row + gzz) : "memory");
+      }
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+  }
+  __syncthreads();
+  const long long n = pg.npart;
+  const long long modulus = (long long)nm << kFracBits;
+  const float inv_one = 1.0f / kWeightOne;
+  bool bad = false;
+#pragma unroll 2
+  for (unsigned e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+    int q[3];
+    long long id;
+    unpack_q(ent_p[e], pg.np, q, &id);
+    const float* sp = KICK ? s : s_in;
+    float sv[3];
+    int c[3];
+    float w1[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      sv[a] = sp[a * n + id];
+      const long long g = fixed_coord(q[a], sv[a], pg.r_fixed, modulus);
+      c[a] = (int)(g >> kFracBits);
+      w1[a] = (float)((int)(g >> (kFracBits - 14)) & (kWeightOne - 1)) * inv_one;
+    }
+    const int lx = c[0] - x0, ly = c[1] - y0, lz = c[2] - z0;   // base cell inside the tile
+    float fr[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int dx = 0; dx < 2; ++dx) {
+      const float wx = dx ? w1[0] : 1.0f - w1[0];
+#pragma unroll
+      for (int dy = 0; dy < 2; ++dy) {
+        const float wxy = wx * (dy ? w1[1] : 1.0f - w1[1]);
+        const int o = ((lx + dx) * hx + (ly + dy)) * hp + lz;
+#pragma unroll
+        for (int comp = 0; comp < 3; ++comp) {
+          const float* p = fsm + comp * (hx * hx * hp) + o;
+          fr[comp] += wxy * ((1.0f - w1[2]) * p[0] + w1[2] * p[1]);
+        }
+      }
+    }
+    if (!KICK) {
+      force_out[id] = fr[0];
+      force_out[n + id] = fr[1];
+      force_out[2 * n + id] = fr[2];
+    } else {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const float p1 = __ldg(psi1 + a * n + id), p2 = __ldg(psi2 + a * n + id);
+        const float fres = fr[a] - (kd.c1 * p1 + kd.c2 * p2);
+        const float vn = v[a * n + id] + kd.kick * fres;
+        const float sn = sv[a] + kd.drift * vn + kd.dd1 * p1 + kd.dd2 * p2;
+        v[a * n + id] = vn;
+        s[a * n + id] = sn;
+        bad |= !isfinite(vn) || !isfinite(sn);
+      }
+    }
+  }
+  if (KICK && __syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flags, 2);
+}
+
+}  // namespace
+
+bool bin_geometry(int nmesh, int np, BinGeom* b) {
+  if (np > 1024) return false;                       // packed 10-bit lattice coordinates
+  int lt = 3;                                        // T = 8 cells across, or the largest power of
+  while (lt > 0 && nmesh % (1 << lt)) --lt;          // two dividing N
+  int lz = 5;                                        // TZ = 32 cells along z, likewise
+  while (lz > 0 && nmesh % (1 << lz)) --lz;
+  if (lz == 0 || lt == 0) return false;
+  b->lt = lt;
+  b->lz = lz;
+  b->nt = nmesh >> lt;
+  b->nz = nmesh >> lz;
+  const long long tiles = (long long)b->nt * b->nt * b->nz;
+  if (tiles > (1LL << 26)) return false;
+  b->tiles = (int)tiles;
+  return true;
+}
+
+size_t bin_smem_bytes(const BinGeom& b, int nmesh) {
+  (void)nmesh;
+  return ((size_t)(1 << b.lt) * (1 << b.lt) << b.lz) * sizeof(unsigned long long);
+}
+
+// z-tiles per gather CTA
+int gather_group(const BinGeom& b) {
+  (void)b;
+  return 1;
+}
+
+size_t gather_smem_bytes(const BinGeom& b) {
+  const size_t hx = (1 << b.lt) + 1, hz = ((size_t)gather_group(b) << b.lz) + 1;
+  const size_t hp = (hz + 3) & ~(size_t)3;
+  return 3 * hx * hx * hp * sizeof(float);
+}
+
+bool tile_gather_pays(const BinGeom& b, long long npart) {
+  // staging a tile's forces costs about as much as gathering a few hundred particles directly;
+  // the 16-byte copies also need rows of at least 4 cells along z
+  const long long groups = (long long)b.tiles / gather_group(b);
+  return b.lz >= 2 && npart >= 384LL * groups;
+}
+
+int launch_binning(const ParticleGeom& pg, const BinGeom& b, const float* s, BinBuffers& bb, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_deposit_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+    cudaFuncSetAttribute(k_gather_tiles<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+    cudaFuncSetAttribute(k_gather_tiles<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+    attr = true;
+  }
+  if (cudaMemsetAsync(bb.cnt_p, 0, (size_t)b.tiles * sizeof(unsigned), st) != cudaSuccess ||
+      cudaMemsetAsync(bb.cnt_s, 0, (size_t)b.tiles * sizeof(unsigned), st) != cudaSuccess)
+    return COLA_ERR_CUDA;
+  const long long rows = (long long)pg.np * pg.np;
+  const unsigned grid = (unsigned)(rows < 152LL * 64 ? rows : 152LL * 64);
+  const int th = pg.np < kThreads ? ((pg.np + 31) / 32) * 32 : kThreads;
+  k_bin<false><<<grid, th, 0, st>>>(pg, b, s, bb.cnt_p, bb.cnt_s, nullptr, nullptr);
+  int e = check_launch("bin_count");
+  if (e != COLA_OK) return e;
+  const int nseg = (b.tiles + kScanSeg - 1) / kScanSeg;
+  k_scan_sums<<<dim3(nseg, 2), kScanThreads, 0, st>>>(bb.cnt_p, bb.cnt_s, b.tiles, bb.seg);
+  k_scan_segs<<<2, kScanThreads, 0, st>>>(bb.seg, nseg);
+  k_scan_apply<<<dim3(nseg, 2), kScanThreads, 0, st>>>(bb.cnt_p, bb.cnt_s, b.tiles, bb.seg, bb.off_p, bb.off_s,
+                                                       bb.cur_p, bb.cur_s);
+  if ((e = check_launch("bin_scan")) != COLA_OK) return e;
+  k_bin<true><<<grid, th, 0, st>>>(pg, b, s, bb.cur_p, bb.cur_s, bb.ent_p, bb.ent_s);
+  return check_launch("bin_scatter");
+}
+
+int launch_deposit_tiles(const ParticleGeom& pg, const BinGeom& b, const float* s, const BinBuffers& bb,
+                         unsigned long long* rho, cudaStream_t st) {
+  k_deposit_tiles<<<b.tiles, kThreads, bin_smem_bytes(b, pg.n), st>>>(pg, b, s, bb.off_p, bb.ent_p, bb.off_s, bb.ent_s,
+                                                                  rho);
+  return check_launch("deposit_tiles");
+}
+
+int launch_gather_tiles(const ParticleGeom& pg, const BinGeom& b, const BinBuffers& bb, const float* const f[3],
+                        long long rs, const float* s_in, float* force_out, float* s, float* v, const float* psi1,
+                        const float* psi2, const KickDrift* kd, int* flags, cudaStream_t st) {
+  const size_t sm = gather_smem_bytes(b);
+  const int gz = gather_group(b);
+  const int blocks = b.tiles / gz;
+  if (kd)
+    k_gather_tiles<true><<<blocks, kThreads, sm, st>>>(pg, b, gz, bb.off_p, bb.ent_p, f[0], f[1], f[2], rs, nullptr,
+                                                        nullptr, s, v, psi1, psi2, *kd, flags);
+  else
+    k_gather_tiles<false><<<blocks, kThreads, sm, st>>>(pg, b, gz, bb.off_p, bb.ent_p, f[0], f[1], f[2], rs, s_in,
+                                                         force_out, nullptr, nullptr, nullptr, nullptr, KickDrift{},
+                                                         flags);
+  return check_launch("gather_tiles");
+}
+
+}  // namespace cola

@@ -76,7 +76,7 @@ void bin_edges(int nmesh, int nbins, long long* e) {
 
 enum Stage {
   kStDeposit = 0, kStFwdZ = 1, kStFwdY = 2, kStGreenX = 3, kStInvY = 4, kStInvZ = 5, kStGather = 6,
-  kStFwdX = 7, kStIc = 8, kStPk = 9, kStClear = 10
+  kStFwdX = 7, kStIc = 8, kStPk = 9, kStClear = 10, kStBin = 11
 };
 
 cudaEvent_t take_event(cola_ctx* c) {
@@ -108,13 +108,37 @@ int staged(cola_ctx* c, int stage, F&& launch) {
 int check_ptr(const void* p) { return (p && ((uintptr_t)p % 16 == 0)) ? COLA_OK : COLA_ERR_INVALID; }
 
 // S1 + S2 (z, y): deposit and the first two forward passes into cbuf[2].
+// S1 into rho: tile-wise (binning, then one plain store per cell) or direct atomics.
+int deposit_mesh(cola_ctx* c, const float* s, unsigned long long* rho) {
+  if (c->binned) {
+    COLA_TRY(STAGED(kStBin, launch_binning(c->pg, c->bg, s, c->bb, c->stream)));
+    return STAGED(kStDeposit, launch_deposit_tiles(c->pg, c->bg, s, c->bb, rho, c->stream));
+  }
+  const size_t n3 = (size_t)c->mesh.n * c->mesh.n * c->mesh.n;
+  COLA_TRY(STAGED(kStClear, cuda_status(cudaMemsetAsync(rho, 0, n3 * sizeof(unsigned long long), c->stream), "memset")));
+  return STAGED(kStDeposit, launch_deposit(c->pg, s, rho, c->flags, c->stream));
+}
+
+// S4 (+S5): gather at the particles deposited by the last deposit_mesh call on the same s.
+int gather(cola_ctx* c, const float* s_in, float* force, float* s, float* v, const float* psi1, const float* psi2,
+           const KickDrift* kd) {
+  const float* f[3] = {reinterpret_cast<float*>(c->cbuf[0]), reinterpret_cast<float*>(c->cbuf[1]),
+                       reinterpret_cast<float*>(c->cbuf[2])};
+  if (c->binned && c->tile_gather)
+    return STAGED(kStGather, launch_gather_tiles(c->pg, c->bg, c->bb, f, 2LL * c->mesh.pc, s_in, force, s, v, psi1,
+                                                 psi2, kd, c->flags, c->stream));
+  return STAGED(kStGather, launch_gather(c->pg, f, 2LL * c->mesh.pc, s_in, force, s, v, psi1, psi2, kd, c->flags,
+                                         c->stream));
+}
+
 int deposit_and_forward_yz(cola_ctx* c, const float* s) {
   const Grid3& g = c->mesh;
   const size_t n3 = (size_t)g.n * g.n * g.n;
-  COLA_TRY(STAGED(kStClear, cuda_status(cudaMemsetAsync(c->rho, 0, n3 * sizeof(unsigned long long), c->stream), "memset")));
-  COLA_TRY(STAGED(kStDeposit, launch_deposit(c->pg, s, c->rho, c->flags, c->stream)));
+  COLA_TRY(deposit_mesh(c, s, c->rho));
   const float scale = (float)((double)n3 / ((double)c->pg.npart * 4398046511104.0));   // N^3 / (n 2^42)
-  COLA_TRY(STAGED(kStFwdZ, launch_r2c_rows(c->mplan, g, kSrcFixedPoint, c->rho, g.n, scale, c->cbuf[2], c->stream)));
+  COLA_TRY(STAGED(kStFwdZ, launch_r2c_rows(c->mplan, g, kSrcFixedPoint, c->rho, g.n, scale, c->cbuf[2], c->stream,
+                                           c->mass_acc)));
+  COLA_TRY(launch_mass_check(c->pg, nullptr, false, c->mass_acc, c->flags, c->stream));
   COLA_TRY(STAGED(kStFwdY, launch_pencils(c->mplan, g, 1, -1, c->cbuf[2], c->stream)));
   return COLA_OK;
 }
@@ -187,7 +211,7 @@ extern "C" void cola_destroy(cola_ctx* c) {
   if (c->edges_host) cudaFreeHost(c->edges_host);
   fft_plan_free(&c->mplan);
   fft_plan_free(&c->lplan);
-  void* bufs[] = {c->arena, c->dtab, c->amp_m2, c->edges, c->pk_partials, c->flags};
+  void* bufs[] = {c->arena, c->dtab, c->amp_m2, c->edges, c->pk_partials, c->flags, c->mass_acc, c->bin_mem};
   for (void* b : bufs)
     if (b) cudaFree(b);
   delete c;
@@ -274,9 +298,32 @@ extern "C" int cola_create(const cola_params* params, void* stream, cola_ctx** o
   if ((st = cuda_status(cudaMalloc(&c->edges, (kPkMaxBins + 1) * sizeof(long long)), "cudaMalloc")) != COLA_OK ||
       (st = cuda_status(cudaMalloc(&c->pk_partials, (size_t)kPkBlocks * 3 * kPkMaxBins * sizeof(double)),
                         "cudaMalloc")) != COLA_OK ||
-      (st = cuda_status(cudaMalloc(&c->flags, sizeof(int)), "cudaMalloc")) != COLA_OK)
+      (st = cuda_status(cudaMalloc(&c->flags, sizeof(int)), "cudaMalloc")) != COLA_OK ||
+      (st = cuda_status(cudaMalloc(&c->mass_acc, 2 * sizeof(unsigned long long)), "cudaMalloc")) != COLA_OK)
     return fail(st);
   cudaMemset(c->flags, 0, sizeof(int));
+  cudaMemset(c->mass_acc, 0, 2 * sizeof(unsigned long long));
+  // tile binning buffers: 6 per-tile arrays, n primary entries and up to 7n spill entries
+  if (bin_geometry(params->nmesh, params->np, &c->bg)) {
+    const size_t tiles = (size_t)c->bg.tiles + 1;
+    const size_t nseg = (tiles + 4095) / 4096 + 1;
+    const size_t bytes = 6 * align256(tiles * sizeof(unsigned)) + align256((size_t)c->pg.npart * 4) +
+                         align256((size_t)c->pg.npart * 28) + align256(2 * nseg * sizeof(unsigned));
+    if ((st = cuda_status(cudaMalloc(&c->bin_mem, bytes), "cudaMalloc bins")) != COLA_OK) return fail(st);
+    char* q = static_cast<char*>(c->bin_mem);
+    unsigned** arr[6] = {&c->bb.cnt_p, &c->bb.cnt_s, &c->bb.off_p, &c->bb.off_s, &c->bb.cur_p, &c->bb.cur_s};
+    for (int i = 0; i < 6; ++i) {
+      *arr[i] = reinterpret_cast<unsigned*>(q);
+      q += align256(tiles * sizeof(unsigned));
+    }
+    c->bb.ent_p = reinterpret_cast<unsigned*>(q);
+    q += align256((size_t)c->pg.npart * 4);
+    c->bb.ent_s = reinterpret_cast<unsigned*>(q);
+    q += align256((size_t)c->pg.npart * 28);
+    c->bb.seg = reinterpret_cast<unsigned*>(q);
+    c->binned = true;
+    c->tile_gather = tile_gather_pays(c->bg, c->pg.npart);
+  }
   if ((st = cuda_status(cudaMallocHost(&c->edges_host, (kPkMaxBins + 1) * sizeof(long long)), "cudaMallocHost")) !=
       COLA_OK)
     return fail(st);
@@ -346,8 +393,9 @@ extern "C" int cola_deposit(cola_ctx* c, const float* s, unsigned long long* rho
   COLA_TRY(check_ptr(s));
   COLA_TRY(check_ptr(rho));
   const size_t n3 = (size_t)c->mesh.n * c->mesh.n * c->mesh.n;
-  COLA_TRY(cuda_status(cudaMemsetAsync(rho, 0, n3 * sizeof(unsigned long long), c->stream), "memset"));
-  return launch_deposit(c->pg, s, rho, c->flags, c->stream);
+  (void)n3;
+  COLA_TRY(deposit_mesh(c, s, rho));
+  return launch_mass_check(c->pg, rho, true, c->mass_acc, c->flags, c->stream);
 }
 
 extern "C" int cola_density_spectrum(cola_ctx* c, const float* s, float* delta_k) {
@@ -364,10 +412,7 @@ extern "C" int cola_pm_force(cola_ctx* c, const float* s, double a, float* force
   COLA_TRY(check_ptr(s));
   COLA_TRY(check_ptr(force));
   COLA_TRY(force_mesh(c, s, 1.5 * c->p.omega_m / a));
-  const float* f[3] = {reinterpret_cast<float*>(c->cbuf[0]), reinterpret_cast<float*>(c->cbuf[1]),
-                       reinterpret_cast<float*>(c->cbuf[2])};
-  return STAGED(kStGather, launch_gather(c->pg, f, 2LL * c->mesh.pc, s, force, nullptr, nullptr, nullptr, nullptr,
-                                         nullptr, c->flags, c->stream));
+  return gather(c, s, force, nullptr, nullptr, nullptr, nullptr, nullptr);
 }
 
 extern "C" int cola_step(cola_ctx* c, int i, float* s, float* v, const float* psi1, const float* psi2) {
@@ -377,10 +422,7 @@ extern "C" int cola_step(cola_ctx* c, int i, float* s, float* v, const float* ps
   const StepScalars& ss = c->steps[i];
   COLA_TRY(force_mesh(c, s, ss.force_scale));
   const KickDrift kd{(float)ss.kick, (float)ss.drift, (float)ss.dd1, (float)ss.dd2, (float)ss.c1, (float)ss.c2};
-  const float* f[3] = {reinterpret_cast<float*>(c->cbuf[0]), reinterpret_cast<float*>(c->cbuf[1]),
-                       reinterpret_cast<float*>(c->cbuf[2])};
-  return STAGED(kStGather, launch_gather(c->pg, f, 2LL * c->mesh.pc, nullptr, nullptr, s, v, psi1, psi2, &kd,
-                                         c->flags, c->stream));
+  return gather(c, nullptr, nullptr, s, v, psi1, psi2, &kd);
 }
 
 extern "C" int cola_power_spectrum(cola_ctx* c, const float* s, double* pk, int nbins) {

@@ -77,7 +77,8 @@ enum RowSource { kSrcFixedPoint = 0, kSrcFloat = 1 };
 // Forward R2C along z of n^2 rows; src is uint64 (scaled: value*scale - 1) or float rows with
 // the given row stride (floats or uint64 elements).  dst: complex grid rows of stride pc.
 int launch_r2c_rows(const FftPlan& p, const Grid3& g, RowSource kind, const void* src,
-                    long long src_row_stride, float scale, float2* dst, cudaStream_t st);
+                    long long src_row_stride, float scale, float2* dst, cudaStream_t st,
+                    unsigned long long* mass_acc = nullptr);
 // Inverse C2R along z, in place on a complex grid (real rows of stride 2*pc floats).
 int launch_c2r_rows(const FftPlan& p, const Grid3& g, float2* data, cudaStream_t st);
 // C2C along y (axis 1) or x (axis 0) of the complex grid; dir = -1 forward, +1 inverse.
@@ -99,6 +100,27 @@ struct ParticleGeom {
 
 int launch_deposit(const ParticleGeom& pg, const float* s, unsigned long long* rho, int* flags,
                    cudaStream_t st);
+// Sets flags bit 0 if the 128-bit total in acc (accumulated by the fixed-point R2C pass, or by
+// summing rho here when sum_mesh) differs from n 2^42, i.e. if some cell wrapped; resets acc.
+int launch_mass_check(const ParticleGeom& pg, const unsigned long long* rho, bool sum_mesh, unsigned long long* acc,
+                      int* flags, cudaStream_t st);
+
+#ifdef __CUDACC__
+// Adds a thread's 128-bit partial (lo, hi) to the global accumulator acc[0..1] (exact, any order).
+// Called by every thread of full warps.
+__device__ __forceinline__ void mass_accumulate(unsigned long long lo, unsigned long long hi, unsigned long long* acc) {
+  for (int off = 16; off > 0; off >>= 1) {
+    const unsigned long long olo = __shfl_down_sync(0xffffffffu, lo, off);
+    const unsigned long long ohi = __shfl_down_sync(0xffffffffu, hi, off);
+    lo += olo;
+    hi += ohi + (lo < olo);
+  }
+  if ((threadIdx.x & 31) == 0 && (lo | hi)) {
+    const unsigned long long old = atomicAdd(acc, lo);
+    atomicAdd(acc + 1, hi + (old + lo < old));
+  }
+}
+#endif
 struct KickDrift {
   float kick, drift, dd1, dd2, c1, c2;
 };
@@ -107,6 +129,31 @@ struct KickDrift {
 int launch_gather(const ParticleGeom& pg, const float* const f[3], long long rs, const float* s_in,
                   float* force_out, float* s, float* v, const float* psi1, const float* psi2,
                   const KickDrift* kd, int* flags, cudaStream_t st);
+
+// Spatial binning by tiles of T x T mesh columns (binning.cu).
+struct BinGeom {
+  int lt;      // log2 T (tile side across z)
+  int lz;      // log2 TZ (tile length along z)
+  int nt;      // tiles per axis across z (N / T)
+  int nz;      // tiles along z (N / TZ)
+  int tiles;   // nt^2 nz
+};
+struct BinBuffers {
+  unsigned *cnt_p = nullptr, *cnt_s = nullptr;   // counts per tile (primary, spill)
+  unsigned *off_p = nullptr, *off_s = nullptr;   // offsets, tiles + 1
+  unsigned *cur_p = nullptr, *cur_s = nullptr;   // scatter cursors
+  unsigned *ent_p = nullptr, *ent_s = nullptr;   // packed lattice coordinates (n primary, up to 7n spill)
+  unsigned* seg = nullptr;                        // scan segment sums (2 lists)
+};
+bool bin_geometry(int nmesh, int np, BinGeom* b);
+size_t bin_smem_bytes(const BinGeom& b, int nmesh);
+bool tile_gather_pays(const BinGeom& b, long long npart);   // else gather in lattice order
+int launch_binning(const ParticleGeom& pg, const BinGeom& b, const float* s, BinBuffers& bb, cudaStream_t st);
+int launch_deposit_tiles(const ParticleGeom& pg, const BinGeom& b, const float* s, const BinBuffers& bb,
+                         unsigned long long* rho, cudaStream_t st);
+int launch_gather_tiles(const ParticleGeom& pg, const BinGeom& b, const BinBuffers& bb, const float* const f[3],
+                        long long rs, const float* s_in, float* force_out, float* s, float* v, const float* psi1,
+                        const float* psi2, const KickDrift* kd, int* flags, cudaStream_t st);
 
 // 2LPT helpers on the lattice grid (side np).
 enum IcField { kIcPsi1 = 0, kIcHess = 1, kIcPsi2 = 2 };
@@ -149,6 +196,12 @@ struct cola_ctx {
   double* pk_partials = nullptr;
   int pk_blocks = 0;
   int* flags = nullptr;                   // sticky device error flags
+  unsigned long long* mass_acc = nullptr; // 128-bit total of the fixed-point mesh (overflow check)
+  bool binned = false;                    // tile-wise deposit (else direct atomics)
+  bool tile_gather = false;               // tile-wise gather from shared memory (else lattice order)
+  cola::BinGeom bg{};
+  cola::BinBuffers bb;
+  void* bin_mem = nullptr;
   // measurement support
   bool prof = false;
   double stage_ms[COLA_NUM_STAGES] = {};

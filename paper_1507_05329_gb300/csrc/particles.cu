@@ -32,128 +32,152 @@ unsigned grid_for(long long work, int threads) {
   return (unsigned)(b < 1 ? 1 : b);
 }
 
-// Fixed-point mesh coordinate of one axis: G = (q R + rint(s 2^20)) mod (N 2^20).
+// Fixed-point mesh coordinate of one axis: G = (q R + rint(s 2^20)) mod (N 2^20).  Displacements
+// below one box length wrap with one compare; larger ones take the modulo path.
 __device__ __forceinline__ long long fixed_coord(int q, float s, long long r_fixed, long long modulus) {
   long long g = (long long)q * r_fixed + __float2ll_rn(s * (float)kFracOne);
-  g %= modulus;
-  return g < 0 ? g + modulus : g;
+  if (g < 0) g += modulus;
+  else if (g >= modulus) g -= modulus;
+  if ((unsigned long long)g >= (unsigned long long)modulus) {
+    g %= modulus;
+    if (g < 0) g += modulus;
+  }
+  return g;
 }
 
-__device__ __forceinline__ void lattice_index(long long id, int np, int* qx, int* qy, int* qz) {
-  const long long np2 = (long long)np * np;
-  *qx = (int)(id / np2);
-  const long long rem = id - (long long)(*qx) * np2;
-  *qy = (int)(rem / np);
-  *qz = (int)(rem - (long long)(*qy) * np);
-}
+// Particles are processed by lattice rows: blockIdx.x (grid-stride) indexes the row (qx, qy) and
+// the threads walk qz, so the lattice index needs one division per row and none per particle.
+constexpr int kRowThreads = 256;
 
-__global__ void k_deposit(ParticleGeom pg, const float* __restrict__ s, unsigned long long* rho,
-                          int* flags) {
+__global__ void __launch_bounds__(kRowThreads) k_deposit(ParticleGeom pg, const float* __restrict__ s,
+                                                        unsigned long long* rho) {
   const long long n = pg.npart;
   const long long modulus = (long long)pg.n << kFracBits;
-  const long long nm = pg.n;
-  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < n;
-       id += (long long)gridDim.x * blockDim.x) {
-    int q[3];
-    lattice_index(id, pg.np, &q[0], &q[1], &q[2]);
-    long long c[3];
-    unsigned long long w1[3], w0[3];
+  const int nm = pg.n, np = pg.np;
+  const long long nrows = (long long)np * np;
+  for (long long row = blockIdx.x; row < nrows; row += gridDim.x) {
+    const int qx = (int)(row / np), qy = (int)(row - (long long)qx * np);
+    for (int qz = threadIdx.x; qz < np; qz += blockDim.x) {
+      const long long id = row * np + qz;
+      const int q[3] = {qx, qy, qz};
+      int c[3];
+      unsigned long long w1[3], w0[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const long long g = fixed_coord(q[a], s[a * n + id], pg.r_fixed, modulus);
-      c[a] = g >> kFracBits;
-      w1[a] = (unsigned long long)((g >> (kFracBits - 14)) & (kWeightOne - 1));
-      w0[a] = kWeightOne - w1[a];
-    }
-    bool over = false;
+      for (int a = 0; a < 3; ++a) {
+        const long long g = fixed_coord(q[a], __ldg(s + a * n + id), pg.r_fixed, modulus);
+        c[a] = (int)(g >> kFracBits);
+        w1[a] = (unsigned long long)((g >> (kFracBits - 14)) & (kWeightOne - 1));
+        w0[a] = kWeightOne - w1[a];
+      }
 #pragma unroll
-    for (int dx = 0; dx < 2; ++dx) {
-      const long long ix = (c[0] + dx) == nm ? 0 : c[0] + dx;
+      for (int dx = 0; dx < 2; ++dx) {
+        const int ix = (c[0] + dx) == nm ? 0 : c[0] + dx;
 #pragma unroll
-      for (int dy = 0; dy < 2; ++dy) {
-        const long long iy = (c[1] + dy) == nm ? 0 : c[1] + dy;
-        const unsigned long long wxy = (dx ? w1[0] : w0[0]) * (dy ? w1[1] : w0[1]);
-        unsigned long long* row = rho + (ix * nm + iy) * nm;
+        for (int dy = 0; dy < 2; ++dy) {
+          const int iy = (c[1] + dy) == nm ? 0 : c[1] + dy;
+          const unsigned long long wxy = (dx ? w1[0] : w0[0]) * (dy ? w1[1] : w0[1]);
+          unsigned long long* rrow = rho + ((long long)ix * nm + iy) * nm;
 #pragma unroll
-        for (int dz = 0; dz < 2; ++dz) {
-          const long long iz = (c[2] + dz) == nm ? 0 : c[2] + dz;
-          const unsigned long long w = wxy * (dz ? w1[2] : w0[2]);
-          if (w) {
-            const unsigned long long old = atomicAdd(row + iz, w);
-            over |= (old + w < old);
+          for (int dz = 0; dz < 2; ++dz) {
+            const int iz = (c[2] + dz) == nm ? 0 : c[2] + dz;
+            const unsigned long long w = wxy * (dz ? w1[2] : w0[2]);
+            if (w) atomicAdd(rrow + iz, w);   // result unused: compiles to a reduction (no return trip)
           }
         }
       }
     }
-    if (over) atomicOr(flags, 1);
   }
 }
 
 // CIC gather of the three force fields, optionally fused with the COLA kick and drift.
 template <bool KICK>
-__global__ void k_gather(ParticleGeom pg, const float* __restrict__ f0, const float* __restrict__ f1,
-                         const float* __restrict__ f2, long long rs, const float* __restrict__ s_in,
-                         float* __restrict__ force_out, float* s, float* v, const float* __restrict__ psi1,
-                         const float* __restrict__ psi2, KickDrift kd, int* flags) {
+__global__ void __launch_bounds__(kRowThreads) k_gather(ParticleGeom pg, const float* __restrict__ f0,
+                                                       const float* __restrict__ f1, const float* __restrict__ f2,
+                                                       long long rs, const float* __restrict__ s_in,
+                                                       float* __restrict__ force_out, float* s, float* v,
+                                                       const float* __restrict__ psi1,
+                                                       const float* __restrict__ psi2, KickDrift kd, int* flags) {
   const long long n = pg.npart;
   const long long modulus = (long long)pg.n << kFracBits;
-  const long long nm = pg.n;
+  const int nm = pg.n, np = pg.np;
+  const long long nrows = (long long)np * np;
   const float inv_one = 1.0f / kWeightOne;
-  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < n;
-       id += (long long)gridDim.x * blockDim.x) {
-    int q[3];
-    lattice_index(id, pg.np, &q[0], &q[1], &q[2]);
-    const float* sp = KICK ? s : s_in;
-    float sv[3];
-    long long c[3];
-    float w1[3];
+  bool bad = false;
+  for (long long row = blockIdx.x; row < nrows; row += gridDim.x) {
+    const int qx = (int)(row / np), qy = (int)(row - (long long)qx * np);
+#pragma unroll 2
+    for (int qz = threadIdx.x; qz < np; qz += blockDim.x) {
+      const long long id = row * np + qz;
+      const int q[3] = {qx, qy, qz};
+      const float* sp = KICK ? s : s_in;
+      float sv[3];
+      int c[3];
+      float w1[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      sv[a] = sp[a * n + id];
-      const long long g = fixed_coord(q[a], sv[a], pg.r_fixed, modulus);
-      c[a] = g >> kFracBits;
-      w1[a] = (float)((g >> (kFracBits - 14)) & (kWeightOne - 1)) * inv_one;
-    }
-    float fx = 0.f, fy = 0.f, fz = 0.f;
+      for (int a = 0; a < 3; ++a) {
+        sv[a] = sp[a * n + id];
+        const long long g = fixed_coord(q[a], sv[a], pg.r_fixed, modulus);
+        c[a] = (int)(g >> kFracBits);
+        w1[a] = (float)((int)(g >> (kFracBits - 14)) & (kWeightOne - 1)) * inv_one;
+      }
+      float fx = 0.f, fy = 0.f, fz = 0.f;
 #pragma unroll
-    for (int dx = 0; dx < 2; ++dx) {
-      const long long ix = (c[0] + dx) == nm ? 0 : c[0] + dx;
-      const float wx = dx ? w1[0] : 1.0f - w1[0];
+      for (int dx = 0; dx < 2; ++dx) {
+        const int ix = (c[0] + dx) == nm ? 0 : c[0] + dx;
+        const float wx = dx ? w1[0] : 1.0f - w1[0];
 #pragma unroll
-      for (int dy = 0; dy < 2; ++dy) {
-        const long long iy = (c[1] + dy) == nm ? 0 : c[1] + dy;
-        const float wxy = wx * (dy ? w1[1] : 1.0f - w1[1]);
-        const long long row = (ix * nm + iy) * rs;
+        for (int dy = 0; dy < 2; ++dy) {
+          const int iy = (c[1] + dy) == nm ? 0 : c[1] + dy;
+          const float wxy = wx * (dy ? w1[1] : 1.0f - w1[1]);
+          const long long rbase = ((long long)ix * nm + iy) * rs;
+          const int iz0 = c[2], iz1 = (c[2] + 1) == nm ? 0 : c[2] + 1;
+          const float wz1 = w1[2], wz0 = 1.0f - w1[2];
+          fx += wxy * (wz0 * __ldg(f0 + rbase + iz0) + wz1 * __ldg(f0 + rbase + iz1));
+          fy += wxy * (wz0 * __ldg(f1 + rbase + iz0) + wz1 * __ldg(f1 + rbase + iz1));
+          fz += wxy * (wz0 * __ldg(f2 + rbase + iz0) + wz1 * __ldg(f2 + rbase + iz1));
+        }
+      }
+      if (!KICK) {
+        force_out[id] = fx;
+        force_out[n + id] = fy;
+        force_out[2 * n + id] = fz;
+      } else {
+        const float fp[3] = {fx, fy, fz};
 #pragma unroll
-        for (int dz = 0; dz < 2; ++dz) {
-          const long long iz = (c[2] + dz) == nm ? 0 : c[2] + dz;
-          const float w = wxy * (dz ? w1[2] : 1.0f - w1[2]);
-          fx += w * __ldg(f0 + row + iz);
-          fy += w * __ldg(f1 + row + iz);
-          fz += w * __ldg(f2 + row + iz);
+        for (int a = 0; a < 3; ++a) {
+          const float p1 = __ldg(psi1 + a * n + id), p2 = __ldg(psi2 + a * n + id);
+          const float fres = fp[a] - (kd.c1 * p1 + kd.c2 * p2);
+          const float vn = v[a * n + id] + kd.kick * fres;
+          const float sn = sv[a] + kd.drift * vn + kd.dd1 * p1 + kd.dd2 * p2;
+          v[a * n + id] = vn;
+          s[a * n + id] = sn;
+          bad |= !isfinite(vn) || !isfinite(sn);
         }
       }
     }
-    if (!KICK) {
-      force_out[id] = fx;
-      force_out[n + id] = fy;
-      force_out[2 * n + id] = fz;
-    } else {
-      const float fp[3] = {fx, fy, fz};
-      bool bad = false;
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        const float p1 = psi1[a * n + id], p2 = psi2[a * n + id];
-        const float fres = fp[a] - (kd.c1 * p1 + kd.c2 * p2);
-        const float vn = v[a * n + id] + kd.kick * fres;
-        const float sn = sv[a] + kd.drift * vn + kd.dd1 * p1 + kd.dd2 * p2;
-        v[a * n + id] = vn;
-        s[a * n + id] = sn;
-        bad |= !isfinite(vn) || !isfinite(sn);
-      }
-      if (bad) atomicOr(flags, 2);
-    }
   }
+  if (KICK && __syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flags, 2);
+}
+
+// Exact overflow check of a fixed-point mesh: the 128-bit sum of the (possibly wrapped) cells
+// equals n 2^42 exactly unless some cell wrapped past 2^64 (each wrap removes 2^64).
+__global__ void k_mass_check(const unsigned long long* __restrict__ acc, unsigned long long expect_lo,
+                             unsigned long long expect_hi, unsigned long long* acc_reset, int* flags) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    if (acc[0] != expect_lo || acc[1] != expect_hi) atomicOr(flags, 1);
+    acc_reset[0] = 0ULL;
+    acc_reset[1] = 0ULL;
+  }
+}
+
+__global__ void k_mesh_sum(const unsigned long long* __restrict__ rho, long long cells, unsigned long long* acc) {
+  unsigned long long lo = 0, hi = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < cells; i += (long long)gridDim.x * blockDim.x) {
+    const unsigned long long v = rho[i];
+    lo += v;
+    hi += (lo < v);
+  }
+  mass_accumulate(lo, hi, acc);
 }
 
 // ---- 2LPT helpers on the lattice grid (side n = np, half spectrum rows of pc) --------------
@@ -349,19 +373,43 @@ __global__ void k_dense_spectrum(int n, int pc, int nc, const float2* __restrict
 
 }  // namespace
 
+unsigned rows_grid(const ParticleGeom& pg) {
+  const long long rows = (long long)pg.np * pg.np;
+  const long long cap = 152LL * 64;
+  return (unsigned)(rows < cap ? rows : cap);
+}
+
 int launch_deposit(const ParticleGeom& pg, const float* s, unsigned long long* rho, int* flags, cudaStream_t st) {
-  k_deposit<<<grid_for(pg.npart, 256), 256, 0, st>>>(pg, s, rho, flags);
+  (void)flags;
+  const int th = pg.np < kRowThreads ? ((pg.np + 31) / 32) * 32 : kRowThreads;
+  k_deposit<<<rows_grid(pg), th, 0, st>>>(pg, s, rho);
   return check_launch("deposit");
+}
+
+int launch_mass_check(const ParticleGeom& pg, const unsigned long long* rho, bool sum_mesh, unsigned long long* acc,
+                      int* flags, cudaStream_t st) {
+  if (sum_mesh) {
+    const long long cells = (long long)pg.n * pg.n * pg.n;
+    k_mesh_sum<<<grid_for(cells, 256), 256, 0, st>>>(rho, cells, acc);
+    const int e = check_launch("mesh_sum");
+    if (e != COLA_OK) return e;
+  }
+  // expected total: n 2^42 as a 128-bit number
+  const unsigned long long n = (unsigned long long)pg.npart;
+  const unsigned long long lo = n << 42, hi = n >> 22;
+  k_mass_check<<<1, 32, 0, st>>>(acc, lo, hi, acc, flags);
+  return check_launch("mass_check");
 }
 
 int launch_gather(const ParticleGeom& pg, const float* const f[3], long long rs, const float* s_in,
                   float* force_out, float* s, float* v, const float* psi1, const float* psi2,
                   const KickDrift* kd, int* flags, cudaStream_t st) {
-  const unsigned g = grid_for(pg.npart, 256);
+  const unsigned g = rows_grid(pg);
+  const int th = pg.np < kRowThreads ? ((pg.np + 31) / 32) * 32 : kRowThreads;
   if (kd)
-    k_gather<true><<<g, 256, 0, st>>>(pg, f[0], f[1], f[2], rs, nullptr, nullptr, s, v, psi1, psi2, *kd, flags);
+    k_gather<true><<<g, th, 0, st>>>(pg, f[0], f[1], f[2], rs, nullptr, nullptr, s, v, psi1, psi2, *kd, flags);
   else
-    k_gather<false><<<g, 256, 0, st>>>(pg, f[0], f[1], f[2], rs, s_in, force_out, nullptr, nullptr, nullptr,
+    k_gather<false><<<g, th, 0, st>>>(pg, f[0], f[1], f[2], rs, s_in, force_out, nullptr, nullptr, nullptr,
                                       nullptr, KickDrift{}, flags);
   return check_launch("gather");
 }

@@ -76,8 +76,10 @@ def test_density_spectrum(npd, nm):
 
 
 # ---- S1-S3 force at particles -----------------------------------------------------------------
-@pytest.mark.parametrize("npd,nm,a", [(16, 32, 0.3), (32, 64, 1.0), (24, 48, 0.5), (20, 40, 0.7)])
+@pytest.mark.parametrize("npd,nm,a", [(16, 32, 0.3), (32, 64, 1.0), (24, 48, 0.5), (20, 40, 0.7),
+                                      (32, 32, 0.6), (48, 48, 0.9), (64, 64, 0.4)])
 def test_pm_force(npd, nm, a):
+    # r = 1 cases are dense enough to take the tile-wise gather from shared memory
     s = cola_inputs.random_displacements(npd, seed=7 * nm, amplitude=1.5)
     ctx = ctx_for(np_side=npd, nmesh=nm, box=100.0)
     f = ctx.pm_force(dev(s), a)
@@ -182,10 +184,11 @@ def test_run_is_bit_reproducible():
         assert torch.equal(a[key], b[key]), key
 
 
-@pytest.mark.parametrize("kw", [dict(ic_mode=1), dict(drift_ansatz=1), dict(nstep=4)])
+@pytest.mark.parametrize("kw", [dict(ic_mode=1), dict(drift_ansatz=1), dict(nstep=4), dict(nmesh=16)])
 def test_run_variants(kw):
     npd = 16
-    cfg = dict(box=128.0, np_side=npd, nmesh=32, **kw)
+    cfg = dict(box=128.0, np_side=npd, nmesh=32)
+    cfg.update(kw)
     wn = cola_inputs.white_noise(npd, seed=9)
     ctx = ctx_for(**cfg)
     out = ctx.run(dev(wn), with_pk=False)
