@@ -16,8 +16,10 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(HERE, "libcola.so")
-SOURCES = ["fft.cu", "particles.cu", "binning.cu", "cola_abi.cu", "cola_static.cu", "host_cosmo.cpp"]
-HEADERS = [os.path.join(CSRC, "cola_internal.h"), os.path.join(ROOT, "include", "cola.h")]
+SOURCES = ["fft.cu", "fft_generic.cu", "fft_fast8.cu", "fft_fast16.cu", "fft_green8.cu", "fft_green16.cu", "particles.cu", "binning.cu", "cola_abi.cu",
+           "cola_static.cu", "host_cosmo.cpp"]
+HEADERS = [os.path.join(CSRC, "cola_internal.h"), os.path.join(CSRC, "fft_core.cuh"), os.path.join(CSRC, "fft_fast.inc"),
+           os.path.join(ROOT, "include", "cola.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include")]
 

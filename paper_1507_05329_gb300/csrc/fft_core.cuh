@@ -1,0 +1,722 @@
+// Device building blocks of the hand-written mixed-radix 3D FFT passes (sm_103a), shared by the
+// FFT translation units.  Hand-written mixed-radix 3D FFT passes for the PM force:
+//
+// The paper's PM force spends 66% of its time in FFTW (§2.3, Table 1).  Here each 1D pass of the
+// 3D transform is one kernel that reads a tile of W pencils from HBM once, transforms it in shared
+// memory with Stockham autosort stages of radix 16/8/5/4/3/2, and writes it once:
+//   * contiguous axis (z): pairs of real rows packed as one complex row (R2C / C2R);
+//   * strided axes (y, x): W adjacent complex columns per tile, so each row segment is a
+//     contiguous W*8-byte run;
+//   * the last forward pass (x) is fused with the Poisson Green function, the 4-point gradient
+//     kernel and the three inverse x transforms of the force components (§2.2 Poisson equation).
+// Shared-memory layout of a tile: element (j, w) at ((j + j/16) * W + w); the skew of one W-row
+// every 16 rows keeps the stride-R writes of the first Stockham stages off a single bank group.
+#pragma once
+#include "cola_internal.h"
+
+#include <cmath>
+#include <cstdio>
+#include <mutex>
+#include <unordered_set>
+
+namespace cola {
+namespace fftk {
+
+constexpr int kEpt = 16;   // complex elements per thread (register staging of a stage)
+constexpr int kMaxThreads = 384;   // largest tile (6144 elements) / kEpt
+
+__device__ __forceinline__ float2 operator+(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 operator-(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 operator*(float s, float2 a) { return make_float2(s * a.x, s * a.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// multiply by -i (forward, DIR < 0) or +i (inverse, DIR > 0)
+template <int DIR>
+__device__ __forceinline__ float2 mul_i(float2 a) {
+  return DIR < 0 ? make_float2(a.y, -a.x) : make_float2(-a.y, a.x);
+}
+template <int DIR>
+__device__ __forceinline__ float2 rot(float2 a, float c, float s) {   // a * (c + i*DIR*s)
+  return DIR < 0 ? make_float2(a.x * c + a.y * s, a.y * c - a.x * s)
+                 : make_float2(a.x * c - a.y * s, a.y * c + a.x * s);
+}
+
+// ---- small DFTs in registers, natural order in and out; sign of the exponent = DIR ----------
+template <int R, int DIR> struct Dft;
+
+template <int DIR> struct Dft<2, DIR> {
+  __device__ __forceinline__ static void run(float2* v) {
+    const float2 t = v[0];
+    v[0] = t + v[1];
+    v[1] = t - v[1];
+  }
+};
+
+template <int DIR> struct Dft<4, DIR> {
+  __device__ __forceinline__ static void run(float2* v) {
+    const float2 t0 = v[0] + v[2], t1 = v[0] - v[2], t2 = v[1] + v[3];
+    const float2 t3 = mul_i<DIR>(v[1] - v[3]);
+    v[0] = t0 + t2;
+    v[2] = t0 - t2;
+    v[1] = t1 + t3;
+    v[3] = t1 - t3;
+  }
+};
+
+template <int DIR> struct Dft<8, DIR> {
+  __device__ __forceinline__ static void run(float2* v) {
+    const float c = 0.70710678118654752f;
+    float2 e[4] = {v[0], v[2], v[4], v[6]};
+    float2 o[4] = {v[1], v[3], v[5], v[7]};
+    Dft<4, DIR>::run(e);
+    Dft<4, DIR>::run(o);
+    o[1] = rot<DIR>(o[1], c, c);
+    o[2] = mul_i<DIR>(o[2]);
+    o[3] = rot<DIR>(o[3], -c, c);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      v[k] = e[k] + o[k];
+      v[k + 4] = e[k] - o[k];
+    }
+  }
+};
+
+template <int DIR> struct Dft<16, DIR> {
+  __device__ __forceinline__ static void run(float2* v) {
+    // w16^k = cos(pi k / 8) + i DIR sin(pi k / 8), k = 0..7
+    const float cs[8] = {1.0f, 0.92387953251128674f, 0.70710678118654752f, 0.38268343236508977f,
+                         0.0f, -0.38268343236508977f, -0.70710678118654752f, -0.92387953251128674f};
+    const float sn[8] = {0.0f, 0.38268343236508977f, 0.70710678118654752f, 0.92387953251128674f,
+                         1.0f, 0.92387953251128674f, 0.70710678118654752f, 0.38268343236508977f};
+    float2 e[8], o[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      e[k] = v[2 * k];
+      o[k] = v[2 * k + 1];
+    }
+    Dft<8, DIR>::run(e);
+    Dft<8, DIR>::run(o);
+#pragma unroll
+    for (int k = 1; k < 8; ++k) o[k] = rot<DIR>(o[k], cs[k], sn[k]);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      v[k] = e[k] + o[k];
+      v[k + 8] = e[k] - o[k];
+    }
+  }
+};
+
+template <int DIR> struct Dft<3, DIR> {
+  __device__ __forceinline__ static void run(float2* v) {
+    const float h = 0.86602540378443865f;   // sqrt(3)/2
+    const float2 s = v[1] + v[2], d = v[1] - v[2];
+    const float2 m = v[0] - 0.5f * s;
+    const float2 t = h * mul_i<DIR>(d);
+    v[0] = v[0] + s;
+    v[1] = m + t;
+    v[2] = m - t;
+  }
+};
+
+template <int DIR> struct Dft<5, DIR> {
+  __device__ __forceinline__ static void run(float2* v) {
+    const float c1 = 0.30901699437494742f, c2 = -0.80901699437494742f;
+    const float s1 = 0.95105651629515357f, s2 = 0.58778525229247313f;
+    const float2 a1 = v[1] + v[4], b1 = v[1] - v[4], a2 = v[2] + v[3], b2 = v[2] - v[3];
+    const float2 m1 = v[0] + c1 * a1 + c2 * a2;
+    const float2 m2 = v[0] + c2 * a1 + c1 * a2;
+    const float2 t1 = mul_i<DIR>(s1 * b1 + s2 * b2);
+    const float2 t2 = mul_i<DIR>(s2 * b1 - s1 * b2);
+    v[0] = v[0] + a1 + a2;
+    v[1] = m1 + t1;
+    v[4] = m1 - t1;
+    v[2] = m2 + t2;
+    v[3] = m2 - t2;
+  }
+};
+
+__device__ __forceinline__ int saddr(int j, int w, int lw) { return ((j + (j >> 4)) << lw) + w; }
+
+// One Stockham stage on W pencils of length n (Govindaraju et al. 2008 formulation): butterfly b
+// reads x[b + r n/R], twiddles by w_n^(r k n/(Ns R)) with k = b mod Ns, and writes
+// y[(b - k) R + k + r Ns].  Ping-pong between two shared buffers, one barrier per stage.
+template <int R, int DIR>
+__device__ __forceinline__ void fft_stage(const float2* __restrict__ x, float2* __restrict__ y, int n, int lw,
+                                          int ns, const float2* __restrict__ tw, int tid, int nthreads) {
+  const int nb = n / R;
+  const int total = nb << lw;
+  const int tstride = n / (ns * R);
+  const int wmask = (1 << lw) - 1;
+  for (int idx = tid; idx < total; idx += nthreads) {
+    const int w = idx & wmask, b = idx >> lw;
+    const int k = b % ns;
+    float2 v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = x[saddr(b + r * nb, w, lw)];
+    if (ns > 1) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        float2 t = __ldg(&tw[r * k * tstride]);
+        if (DIR > 0) t.y = -t.y;
+        v[r] = cmul(v[r], t);
+      }
+    }
+    Dft<R, DIR>::run(v);
+    const int base = (b - k) * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) y[saddr(base + r * ns, w, lw)] = v[r];
+  }
+  __syncthreads();
+}
+
+// All stages of the plan; the data starts in buffer a and the returned pointer holds the result.
+template <int DIR>
+__device__ float2* fft_smem(float2* a, float2* b, const FftDev& p, int lw, int tid, int nthreads) {
+  int ns = 1;
+  for (int st = 0; st < p.nstages; ++st) {
+    const int r = p.radix[st];
+    switch (r) {
+      case 16: fft_stage<16, DIR>(a, b, p.n, lw, ns, p.tw, tid, nthreads); break;
+      case 8: fft_stage<8, DIR>(a, b, p.n, lw, ns, p.tw, tid, nthreads); break;
+      case 5: fft_stage<5, DIR>(a, b, p.n, lw, ns, p.tw, tid, nthreads); break;
+      case 4: fft_stage<4, DIR>(a, b, p.n, lw, ns, p.tw, tid, nthreads); break;
+      case 3: fft_stage<3, DIR>(a, b, p.n, lw, ns, p.tw, tid, nthreads); break;
+      default: fft_stage<2, DIR>(a, b, p.n, lw, ns, p.tw, tid, nthreads); break;
+    }
+    float2* t = a;
+    a = b;
+    b = t;
+    ns *= r;
+  }
+  return a;
+}
+
+__device__ __forceinline__ int tile_elems(int n, int lw) { return (n + n / 16 + 1) << lw; }
+
+// =============================================================================================
+// Fast path: plans whose every stage has ns = (product of earlier radices) a power of two, i.e.
+// n = 2^a * (1, 3 or 5) with the odd factor as the last stage.  No runtime division; the first
+// stage loads from global memory into registers and the last stage stores from registers.
+// Inverse transforms run the transposed stages in reverse order with conjugate twiddles
+// (F is symmetric, so conj(F) = conj(S_0^T) ... conj(S_{m-1}^T)); the first of them reads exactly
+// the elements the forward's last butterfly produced, which keeps the Green multiply in registers.
+// =============================================================================================
+struct FastPlan {
+  int n, nst;
+  int radix[kMaxStages];
+  int lns[kMaxStages];    // log2 of ns at each stage
+  int tstr[kMaxStages];   // twiddle stride n / (ns R)
+  const float2* tw;
+};
+
+template <int DIR>
+__device__ __forceinline__ float2 twid(const float2* __restrict__ tw, int t) {
+  float2 v = __ldg(&tw[t]);
+  if (DIR > 0) v.y = -v.y;
+  return v;
+}
+
+// Pencil pairs: with two or more pencils per tile a thread takes the same butterfly of two
+// adjacent pencils, so the twiddles and index arithmetic are shared and every shared/global
+// access moves 16 bytes.
+__device__ __forceinline__ float4 pack2(float2 a, float2 b) { return make_float4(a.x, a.y, b.x, b.y); }
+
+template <int R, int DIR, class Src, class Dst, int EPT>
+__device__ __forceinline__ void fwd_stage_pairs(const FastPlan& p, int s, int lw, const Src& src, const Dst& dst,
+                                                int tid, int nthreads) {
+  constexpr int kB = (EPT + 2 * R - 1) / (2 * R);
+  const int nb = p.n / R, lwp = lw - 1, total = nb << lwp, lns = p.lns[s], tstr = p.tstr[s];
+  const int wm = (1 << lwp) - 1, km = (1 << lns) - 1;
+#pragma unroll
+  for (int i = 0; i < kB; ++i) {
+    const int idx = tid + i * nthreads;
+    if (idx < total) {
+      const int w = (idx & wm) << 1, b = idx >> lwp, k = b & km;
+      float2 va[R], vb[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const float4 q = src.ld2(b + r * nb, w);
+        va[r] = make_float2(q.x, q.y);
+        vb[r] = make_float2(q.z, q.w);
+      }
+      if (lns) {
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          const float2 t = twid<DIR>(p.tw, r * k * tstr);
+          va[r] = cmul(va[r], t);
+          vb[r] = cmul(vb[r], t);
+        }
+      }
+      Dft<R, DIR>::run(va);
+      Dft<R, DIR>::run(vb);
+      const int base = (((b >> lns) * R) << lns) + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) dst.st2(base + (r << lns), w, pack2(va[r], vb[r]));
+    }
+  }
+}
+
+template <int R, int DIR, class Src, class Dst, int EPT>
+__device__ __forceinline__ void tr_stage_pairs(const FastPlan& p, int s, int lw, const Src& src, const Dst& dst,
+                                               int tid, int nthreads) {
+  constexpr int kB = (EPT + 2 * R - 1) / (2 * R);
+  const int nb = p.n / R, lwp = lw - 1, total = nb << lwp, lns = p.lns[s], tstr = p.tstr[s];
+  const int wm = (1 << lwp) - 1, km = (1 << lns) - 1;
+#pragma unroll
+  for (int i = 0; i < kB; ++i) {
+    const int idx = tid + i * nthreads;
+    if (idx < total) {
+      const int w = (idx & wm) << 1, b = idx >> lwp, k = b & km;
+      const int base = (((b >> lns) * R) << lns) + k;
+      float2 va[R], vb[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const float4 q = src.ld2(base + (r << lns), w);
+        va[r] = make_float2(q.x, q.y);
+        vb[r] = make_float2(q.z, q.w);
+      }
+      Dft<R, DIR>::run(va);
+      Dft<R, DIR>::run(vb);
+      if (lns) {
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          const float2 t = twid<DIR>(p.tw, r * k * tstr);
+          va[r] = cmul(va[r], t);
+          vb[r] = cmul(vb[r], t);
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < R; ++r) dst.st2(b + r * nb, w, pack2(va[r], vb[r]));
+    }
+  }
+}
+
+// forward (decimation in time) stage s
+template <int R, int DIR, class Src, class Dst, int EPT = kEpt>
+__device__ __forceinline__ void fwd_stage(const FastPlan& p, int s, int lw, const Src& src, const Dst& dst, int tid,
+                                          int nthreads) {
+  if (R <= 8 && lw >= 1) {
+    fwd_stage_pairs<R, DIR, Src, Dst, EPT>(p, s, lw, src, dst, tid, nthreads);
+    return;
+  }
+  constexpr int kB = (EPT + R - 1) / R;
+  const int nb = p.n / R, total = nb << lw, lns = p.lns[s], tstr = p.tstr[s];
+  const int wm = (1 << lw) - 1, km = (1 << lns) - 1;
+#pragma unroll
+  for (int i = 0; i < kB; ++i) {
+    const int idx = tid + i * nthreads;
+    if (idx < total) {
+      const int w = idx & wm, b = idx >> lw, k = b & km;
+      float2 v[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[r] = src(b + r * nb, w);
+      if (lns) {
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[r] = cmul(v[r], twid<DIR>(p.tw, r * k * tstr));
+      }
+      Dft<R, DIR>::run(v);
+      const int base = (((b >> lns) * R) << lns) + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) dst(base + (r << lns), w, v[r]);
+    }
+  }
+}
+
+// transposed stage s (used in reverse order for the inverse transform)
+template <int R, int DIR, class Src, class Dst, int EPT = kEpt>
+__device__ __forceinline__ void tr_stage(const FastPlan& p, int s, int lw, const Src& src, const Dst& dst, int tid,
+                                         int nthreads) {
+  if (R <= 8 && lw >= 1) {
+    tr_stage_pairs<R, DIR, Src, Dst, EPT>(p, s, lw, src, dst, tid, nthreads);
+    return;
+  }
+  constexpr int kB = (EPT + R - 1) / R;
+  const int nb = p.n / R, total = nb << lw, lns = p.lns[s], tstr = p.tstr[s];
+  const int wm = (1 << lw) - 1, km = (1 << lns) - 1;
+#pragma unroll
+  for (int i = 0; i < kB; ++i) {
+    const int idx = tid + i * nthreads;
+    if (idx < total) {
+      const int w = idx & wm, b = idx >> lw, k = b & km;
+      const int base = (((b >> lns) * R) << lns) + k;
+      float2 v[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[r] = src(base + (r << lns), w);
+      Dft<R, DIR>::run(v);
+      if (lns) {
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[r] = cmul(v[r], twid<DIR>(p.tw, r * k * tstr));
+      }
+#pragma unroll
+      for (int r = 0; r < R; ++r) dst(b + r * nb, w, v[r]);
+    }
+  }
+}
+
+// MAXR: the largest radix the kernel is compiled for (8 or 16); radix-16 code is left out of the
+// kernels of plans that do not use it, which keeps their register count down.
+template <bool TR, int DIR, int MAXR, class Src, class Dst>
+__device__ __forceinline__ void any_stage(const FastPlan& p, int s, int lw, const Src& src, const Dst& dst, int tid,
+                                          int nt) {
+  switch (p.radix[s]) {
+    case 16:
+      if constexpr (MAXR >= 16) {
+        TR ? tr_stage<16, DIR>(p, s, lw, src, dst, tid, nt) : fwd_stage<16, DIR>(p, s, lw, src, dst, tid, nt);
+      }
+      break;
+    case 8: TR ? tr_stage<8, DIR>(p, s, lw, src, dst, tid, nt) : fwd_stage<8, DIR>(p, s, lw, src, dst, tid, nt); break;
+    case 5: TR ? tr_stage<5, DIR>(p, s, lw, src, dst, tid, nt) : fwd_stage<5, DIR>(p, s, lw, src, dst, tid, nt); break;
+    case 4: TR ? tr_stage<4, DIR>(p, s, lw, src, dst, tid, nt) : fwd_stage<4, DIR>(p, s, lw, src, dst, tid, nt); break;
+    case 3: TR ? tr_stage<3, DIR>(p, s, lw, src, dst, tid, nt) : fwd_stage<3, DIR>(p, s, lw, src, dst, tid, nt); break;
+    default: TR ? tr_stage<2, DIR>(p, s, lw, src, dst, tid, nt) : fwd_stage<2, DIR>(p, s, lw, src, dst, tid, nt); break;
+  }
+}
+
+template <bool TR, int DIR, int MAXR, int EPT, class Src, class Dst>
+__device__ __forceinline__ void any_stage_e(const FastPlan& p, int s, int lw, const Src& src, const Dst& dst, int tid,
+                                            int nt) {
+  switch (p.radix[s]) {
+    case 16:
+      if constexpr (MAXR >= 16) {
+        TR ? tr_stage<16, DIR, Src, Dst, EPT>(p, s, lw, src, dst, tid, nt)
+           : fwd_stage<16, DIR, Src, Dst, EPT>(p, s, lw, src, dst, tid, nt);
+      }
+      break;
+    case 8: TR ? tr_stage<8, DIR, Src, Dst, EPT>(p, s, lw, src, dst, tid, nt) : fwd_stage<8, DIR, Src, Dst, EPT>(p, s, lw, src, dst, tid, nt); break;
+    case 5: TR ? tr_stage<5, DIR, Src, Dst, EPT>(p, s, lw, src, dst, tid, nt) : fwd_stage<5, DIR, Src, Dst, EPT>(p, s, lw, src, dst, tid, nt); break;
+    case 4: TR ? tr_stage<4, DIR, Src, Dst, EPT>(p, s, lw, src, dst, tid, nt) : fwd_stage<4, DIR, Src, Dst, EPT>(p, s, lw, src, dst, tid, nt); break;
+    case 3: TR ? tr_stage<3, DIR, Src, Dst, EPT>(p, s, lw, src, dst, tid, nt) : fwd_stage<3, DIR, Src, Dst, EPT>(p, s, lw, src, dst, tid, nt); break;
+    default: TR ? tr_stage<2, DIR, Src, Dst, EPT>(p, s, lw, src, dst, tid, nt) : fwd_stage<2, DIR, Src, Dst, EPT>(p, s, lw, src, dst, tid, nt); break;
+  }
+}
+
+struct SmemR {
+  const float2* s;
+  int lw;
+  __device__ __forceinline__ float2 operator()(int j, int w) const { return s[saddr(j, w, lw)]; }
+  __device__ __forceinline__ float4 ld2(int j, int w) const {
+    return *reinterpret_cast<const float4*>(s + saddr(j, w, lw));
+  }
+};
+struct SmemW {
+  float2* s;
+  int lw;
+  __device__ __forceinline__ void operator()(int j, int w, float2 v) const { s[saddr(j, w, lw)] = v; }
+  __device__ __forceinline__ void st2(int j, int w, float4 v) const {
+    *reinterpret_cast<float4*>(s + saddr(j, w, lw)) = v;
+  }
+};
+
+// Forward transform of a tile: stage 0 reads gsrc, the last stage writes gdst, shared memory
+// (buffers a, b) in between.  Ends with a barrier only when the caller asks (sync_end).
+template <int DIR, int MAXR, class GSrc, class GDst>
+__device__ __forceinline__ void fwd_tile(const FastPlan& p, int lw, float2* a, float2* b, const GSrc& gsrc,
+                                         const GDst& gdst, int tid, int nt) {
+  const int m = p.nst;
+  if (m == 1) {
+    any_stage<false, DIR, MAXR>(p, 0, lw, gsrc, gdst, tid, nt);
+    return;
+  }
+  any_stage<false, DIR, MAXR>(p, 0, lw, gsrc, SmemW{a, lw}, tid, nt);
+  __syncthreads();
+  for (int s = 1; s < m - 1; ++s) {
+    any_stage<false, DIR, MAXR>(p, s, lw, SmemR{a, lw}, SmemW{b, lw}, tid, nt);
+    __syncthreads();
+    float2* t = a;
+    a = b;
+    b = t;
+  }
+  any_stage<false, DIR, MAXR>(p, m - 1, lw, SmemR{a, lw}, gdst, tid, nt);
+}
+
+// Inverse transform of a tile by the transposed stages m-1 .. 0.
+template <int DIR, int MAXR, class GSrc, class GDst>
+__device__ __forceinline__ void inv_tile(const FastPlan& p, int lw, float2* a, float2* b, const GSrc& gsrc,
+                                         const GDst& gdst, int tid, int nt) {
+  const int m = p.nst;
+  if (m == 1) {
+    any_stage<true, DIR, MAXR>(p, 0, lw, gsrc, gdst, tid, nt);
+    return;
+  }
+  any_stage<true, DIR, MAXR>(p, m - 1, lw, gsrc, SmemW{a, lw}, tid, nt);
+  __syncthreads();
+  for (int s = m - 2; s > 0; --s) {
+    any_stage<true, DIR, MAXR>(p, s, lw, SmemR{a, lw}, SmemW{b, lw}, tid, nt);
+    __syncthreads();
+    float2* t = a;
+    a = b;
+    b = t;
+  }
+  any_stage<true, DIR, MAXR>(p, 0, lw, SmemR{a, lw}, gdst, tid, nt);
+}
+
+// ---- global-memory views ---------------------------------------------------------------------
+struct PencilG {   // W adjacent columns of a strided pencil, masked beyond nc
+  float2* base;
+  long long jstride;
+  int cols_left;   // nc - col0
+  __device__ __forceinline__ float2 operator()(int j, int w) const {
+    return w < cols_left ? base[j * jstride + w] : make_float2(0.f, 0.f);
+  }
+  __device__ __forceinline__ void operator()(int j, int w, float2 v) const {
+    if (w < cols_left) base[j * jstride + w] = v;
+  }
+  __device__ __forceinline__ float4 ld2(int j, int w) const {
+    if (w + 1 < cols_left) return *reinterpret_cast<const float4*>(base + j * jstride + w);
+    return pack2((*this)(j, w), (*this)(j, w + 1));
+  }
+  __device__ __forceinline__ void st2(int j, int w, float4 v) const {
+    if (w + 1 < cols_left) *reinterpret_cast<float4*>(base + j * jstride + w) = v;
+    else if (w < cols_left) base[j * jstride + w] = make_float2(v.x, v.y);
+  }
+};
+
+template <int SRC>
+struct RowPairSrc {   // complex (row 2w, row 2w+1) at column j of real rows
+  const void* src;
+  long long rs, row0, nrows;
+  float scale;
+  mutable unsigned long long mlo = 0, mhi = 0;   // 128-bit sum of the fixed-point values read
+  __device__ __forceinline__ float2 operator()(int j, int w) const {
+    const long long ra = row0 + 2 * w;
+    float a = 0.f, b = 0.f;
+    if (SRC == kSrcFixedPoint) {
+      const unsigned long long* s = static_cast<const unsigned long long*>(src);
+      if (ra < nrows) {
+        const unsigned long long va = s[ra * rs + j];
+        a = __ull2float_rn(va) * scale - 1.0f;
+        mlo += va;
+        mhi += (mlo < va);
+      }
+      if (ra + 1 < nrows) {
+        const unsigned long long vb = s[(ra + 1) * rs + j];
+        b = __ull2float_rn(vb) * scale - 1.0f;
+        mlo += vb;
+        mhi += (mlo < vb);
+      }
+    } else {
+      const float* s = static_cast<const float*>(src);
+      if (ra < nrows) a = s[ra * rs + j] * scale;
+      if (ra + 1 < nrows) b = s[(ra + 1) * rs + j] * scale;
+    }
+    return make_float2(a, b);
+  }
+  __device__ __forceinline__ float4 ld2(int j, int w) const { return pack2((*this)(j, w), (*this)(j, w + 1)); }
+};
+
+struct HalfPairSrc {   // C[k] = A[k] + i B[k] of two Hermitian half rows (C2R input)
+  const float2* data;
+  int pc, n;
+  long long row0, nrows;
+  __device__ __forceinline__ float2 operator()(int k, int w) const {
+    const long long ra = row0 + 2 * w;
+    const int nh = n / 2;
+    const int kk = k <= nh ? k : n - k;
+    float2 A = make_float2(0.f, 0.f), B = make_float2(0.f, 0.f);
+    if (ra < nrows) A = data[ra * pc + kk];
+    if (ra + 1 < nrows) B = data[(ra + 1) * pc + kk];
+    if (kk == 0 || kk == nh) {
+      A.y = 0.f;
+      B.y = 0.f;
+    }
+    return k <= nh ? make_float2(A.x - B.y, A.y + B.x) : make_float2(A.x + B.y, B.x - A.y);
+  }
+  __device__ __forceinline__ float4 ld2(int k, int w) const { return pack2((*this)(k, w), (*this)(k, w + 1)); }
+};
+
+struct RealPairDst {   // (re, im) -> real rows (2w, 2w+1)
+  float* out;
+  long long rs, row0, nrows;
+  __device__ __forceinline__ void operator()(int j, int w, float2 v) const {
+    const long long ra = row0 + 2 * w;
+    if (ra < nrows) out[ra * rs + j] = v.x;
+    if (ra + 1 < nrows) out[(ra + 1) * rs + j] = v.y;
+  }
+  __device__ __forceinline__ void st2(int j, int w, float4 v) const {
+    (*this)(j, w, make_float2(v.x, v.y));
+    (*this)(j, w + 1, make_float2(v.z, v.w));
+  }
+};
+
+__device__ __forceinline__ int fast_tile_elems(int n, int lw) { return (n + n / 16 + 1) << lw; }
+
+// x pass fused with Green function and gradient kernel, spectrum kept in registers between the
+// forward transform's last stage and the inverse transforms' first (transposed) stage.
+template <int RL, int MAXR>
+__device__ __forceinline__ void green_body(const FastPlan& p, int lw, const float2* in, float2* out0, float2* out1,
+                                           float2* out2, int pc, int nc, const float* __restrict__ dtab,
+                                           float g_scale) {
+  extern __shared__ float2 sm[];
+  constexpr int kB = (kEpt + RL - 1) / RL;
+  const int n = p.n, tid = threadIdx.x, nt = blockDim.x, m = p.nst;
+  const int col0 = blockIdx.x << lw, y = blockIdx.y;
+  const long long jstride = (long long)n * pc;
+  const long long boff = (long long)y * pc + col0;
+  float2* a = sm;
+  float2* b = sm + fast_tile_elems(n, lw);
+  const PencilG gin{const_cast<float2*>(in) + boff, jstride, nc - col0};
+  const int nb = n / RL, total = nb << lw, wm = (1 << lw) - 1;
+  const int ls = p.lns[m - 1], tstr = p.tstr[m - 1];
+  float2 spec[kB][RL];
+  // forward stages 0 .. m-2 (shared memory), last stage into registers
+  const float2* last_in = nullptr;
+  if (m > 1) {
+    any_stage<false, -1, MAXR>(p, 0, lw, gin, SmemW{a, lw}, tid, nt);
+    __syncthreads();
+    for (int s = 1; s < m - 1; ++s) {
+      any_stage<false, -1, MAXR>(p, s, lw, SmemR{a, lw}, SmemW{b, lw}, tid, nt);
+      __syncthreads();
+      float2* t = a;
+      a = b;
+      b = t;
+    }
+    last_in = a;
+  }
+#pragma unroll
+  for (int i = 0; i < kB; ++i) {
+    const int idx = tid + i * nt;
+    if (idx < total) {
+      const int w = idx & wm, bb = idx >> lw;   // last stage: bb < ns, k = bb
+#pragma unroll
+      for (int r = 0; r < RL; ++r) spec[i][r] = m > 1 ? last_in[saddr(bb + r * nb, w, lw)] : gin(bb + r * nb, w);
+      if (ls) {
+#pragma unroll
+        for (int r = 1; r < RL; ++r) spec[i][r] = cmul(spec[i][r], twid<-1>(p.tw, r * bb * tstr));
+      }
+      Dft<RL, -1>::run(spec[i]);
+      // element j = bb + r*ns_last: multiply by g_scale / |m|^2 (the common factor of F_j)
+      const int my = y < n / 2 ? y : y - n, mz = col0 + w;
+#pragma unroll
+      for (int r = 0; r < RL; ++r) {
+        const int j = bb + (r << ls);
+        const int mx = j < n / 2 ? j : j - n;
+        const int m2 = mx * mx + my * my + mz * mz;
+        spec[i][r] = (m2 > 0 ? g_scale / (float)m2 : 0.0f) * spec[i][r];
+      }
+    }
+  }
+  __syncthreads();   // the forward's shared buffers are free from here on
+  const float dy = dtab[y];
+  a = sm;
+  b = sm + fast_tile_elems(n, lw);
+#pragma unroll 1
+  for (int comp = 0; comp < 3; ++comp) {
+    float2* o = comp == 0 ? out0 : (comp == 1 ? out1 : out2);
+    const PencilG gout{o + boff, jstride, nc - col0};
+    float2* cur = a;
+    float2* nxt = b;
+#pragma unroll
+    for (int i = 0; i < kB; ++i) {
+      const int idx = tid + i * nt;
+      if (idx < total) {
+        const int w = idx & wm, bb = idx >> lw;
+        const int mz = col0 + w;
+        float2 v[RL];
+#pragma unroll
+        for (int r = 0; r < RL; ++r) {
+          const int j = bb + (r << ls);
+          const float d = comp == 0 ? dtab[j] : (comp == 1 ? dy : (mz < nc ? dtab[mz] : 0.0f));
+          v[r] = make_float2(-d * spec[i][r].y, d * spec[i][r].x);   // i D g delta
+        }
+        // transposed last stage (first of the inverse): inputs are exactly v
+        Dft<RL, +1>::run(v);
+        if (ls) {
+#pragma unroll
+          for (int r = 1; r < RL; ++r) v[r] = cmul(v[r], twid<+1>(p.tw, r * bb * tstr));
+        }
+#pragma unroll
+        for (int r = 0; r < RL; ++r) {
+          if (m > 1) cur[saddr(bb + r * nb, w, lw)] = v[r];
+          else gout(bb + r * nb, w, v[r]);
+        }
+      }
+    }
+    if (m > 1) {
+      __syncthreads();
+      for (int s = m - 2; s > 0; --s) {
+        any_stage<true, +1, MAXR>(p, s, lw, SmemR{cur, lw}, SmemW{nxt, lw}, tid, nt);
+        __syncthreads();
+        float2* t = cur;
+        cur = nxt;
+        nxt = t;
+      }
+      any_stage<true, +1, MAXR>(p, 0, lw, SmemR{cur, lw}, gout, tid, nt);
+      __syncthreads();   // before the next component reuses the buffers
+    }
+  }
+}
+
+// =============================================================================================
+// Persistent, software-pipelined strided passes.  Each CTA walks tiles t = blockIdx.x + i gridDim.x.
+// The tile's W columns are fetched with cp.async (16-byte chunks, zero fill beyond nc) into a
+// staging buffer S; after stage 0 has consumed S the copy of the next tile is issued, so the HBM
+// reads of tile i+1 overlap the shared-memory stages and the global stores of tile i.
+// =============================================================================================
+constexpr int kPipeEpt = 16;             // complex elements per thread per stage
+constexpr int kPipeThreads = 768;
+
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc, int bytes) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gsrc), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Issue the copy of tile (chunk, outer) into S: n rows of W complex, as W/2 16-byte pieces per row.
+__device__ __forceinline__ void fetch_tile(float2* S, const float2* data, long long jstride, long long ostride, int nc,
+                                           int n, int lw, int chunk, int outer, int tid, int nt) {
+  const int W = 1 << lw, col0 = chunk << lw;
+  const float2* base = data + (long long)outer * ostride + col0;
+  const int pieces = n * (W >> 1);
+  for (int q = tid; q < pieces; q += nt) {
+    const int j = q / (W >> 1), w = (q - j * (W >> 1)) * 2;
+    const int valid = nc - col0 - w;   // complex values available from this column on
+    const int bytes = valid >= 2 ? 16 : (valid == 1 ? 8 : 0);
+    cp_async16(S + saddr(j, w, lw), bytes ? (const void*)(base + j * jstride + w) : (const void*)base, bytes);
+  }
+  cp_async_commit();
+}
+
+
+// Raises a kernel's dynamic shared-memory limit the first time it is launched (host side).
+template <class K>
+inline void ensure_smem(K kernel) {
+  static std::mutex mu;
+  static std::unordered_set<const void*> done;
+  std::lock_guard<std::mutex> lock(mu);
+  const void* key = reinterpret_cast<const void*>(kernel);
+  if (done.insert(key).second) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+}
+
+}  // namespace fftk
+
+// Launchers of the kernels compiled in the separate FFT translation units.
+template <int MAXR>
+void fast_r2c_launch(const fftk::FastPlan& fp, int lw, unsigned blocks, int threads, size_t smem, int kind,
+                     const void* src, long long rs, float scale, float2* dst, int pc, long long nrows,
+                     unsigned long long* acc, cudaStream_t st);
+template <int MAXR>
+void fast_c2r_launch(const fftk::FastPlan& fp, int lw, unsigned blocks, int threads, size_t smem, float2* data, int pc,
+                     long long nrows, cudaStream_t st);
+template <int MAXR>
+void fast_pencils_launch(const fftk::FastPlan& fp, int lw, dim3 grid, int threads, size_t smem, int dir, float2* data,
+                         long long jstride, long long ostride, int nc, cudaStream_t st);
+template <int MAXR>
+void fast_green_launch(const fftk::FastPlan& fp, int lw, dim3 grid, int threads, size_t smem, const float2* in,
+                       float2* const out[3], int pc, int nc, const float* dtab, float g_scale, cudaStream_t st);
+template <int MAXR>
+void pipe_pencils_launch(const fftk::FastPlan& fp, int lw, int ctas, int threads, size_t smem, int dir, float2* data,
+                         long long jstride, long long ostride, int nc, int nchunks, int ntiles, cudaStream_t st);
+void generic_r2c_launch(const FftDev& d, int lw, unsigned blocks, int threads, size_t smem, int kind, const void* src,
+                        long long rs, float scale, float2* dst, int pc, long long nrows, unsigned long long* acc,
+                        cudaStream_t st);
+void generic_c2r_launch(const FftDev& d, int lw, unsigned blocks, int threads, size_t smem, float2* data, int pc,
+                        long long nrows, cudaStream_t st);
+void generic_pencils_launch(const FftDev& d, int lw, dim3 grid, int threads, size_t smem, int dir, float2* data,
+                            long long jstride, long long ostride, int nc, cudaStream_t st);
+void generic_green_launch(const FftDev& d, int lw, dim3 grid, int threads, size_t smem, const float2* in,
+                          float2* const out[3], int pc, int nc, const float* dtab, float g_scale, cudaStream_t st);
+void generic_set_smem_limits();
+
+}  // namespace cola

@@ -1,0 +1,5 @@
+// Fused Green-function FFT kernels for plans whose largest radix is 8.
+#define COLA_MAXR 8
+#define COLA_PART_MAIN 0
+#define COLA_PART_GREEN 1
+#include "fft_fast.inc"
