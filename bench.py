@@ -56,6 +56,25 @@ def dist_env():
     return ws, int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0"))
 
 
+# ---- replicas: one independent realisation per rank, no collective on the data path ---------------
+def replica_seed(base_seed: int, rank: int) -> int:
+    """Seed of rank's realisation: independent white noise per replica."""
+    return base_seed + 1000 * rank
+
+
+def slowest_rank_ms(ms: float, dist, device) -> float:
+    """Max over ranks of a per-rank time (the only collective: one scalar after the timed region)."""
+    import torch
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, particles: int, nstep: int, ms: float) -> float:
+    """Particle-steps per second of all replicas together, timed by the slowest rank."""
+    return world * particles * nstep / (ms / 1e3)
+
+
 # ---- algorithmic bytes per launch of each stage (mesh N, particles n) ---------------------------
 def stage_bytes(n_mesh: int, n_part: int) -> dict:
     nc = n_mesh // 2 + 1
@@ -208,7 +227,7 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     build.build()
     w = WORKLOADS[args.workload]
-    seed = w["seed"] + 1000 * rank
+    seed = replica_seed(w["seed"], rank)
     p = Params(box=w["box"], np_side=w["np_side"], nmesh=w["nmesh"], nstep=10)
     n = p.n
     stream = torch.cuda.current_stream()
@@ -244,10 +263,8 @@ def run_ours(args):
     ctx.profile(False)
     ms = e0.elapsed_time(e1) / args.steps
     if ws > 1:
-        t = torch.tensor([ms], device=f"cuda:{local}", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = ws * n * p.nstep / (ms / 1e3)
+        ms = slowest_rank_ms(ms, dist, f"cuda:{local}")
+    value = whole_job_rate(ws, n, p.nstep, ms)
 
     # roofline of the dominant PM-step kernel
     sb = stage_bytes(p.nmesh, n)
@@ -302,10 +319,8 @@ def run_ours(args):
             torch.cuda.synchronize()
         t_e2e = (time.perf_counter() - t0) / args.e2e_steps
         if ws > 1:
-            t = torch.tensor([t_e2e], device=f"cuda:{local}", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            t_e2e = float(t.item())
-        e2e = {"value": ws * n * p.nstep / t_e2e, "unit": UNIT, "h2d_bytes_per_step": 4 * n,
+            t_e2e = slowest_rank_ms(t_e2e * 1e3, dist, f"cuda:{local}") / 1e3
+        e2e = {"value": whole_job_rate(ws, n, p.nstep, t_e2e * 1e3), "unit": UNIT, "h2d_bytes_per_step": 4 * n,
                "d2h_bytes_per_step": 24 * n + 24 * args.nbins, "steps": args.e2e_steps,
                "ms_per_step": t_e2e * 1e3}
         del wn_host, s_host, v_host, pk_host

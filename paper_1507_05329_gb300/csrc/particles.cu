@@ -274,8 +274,9 @@ constexpr int kPkWarps = kPkThreads / 32;
 constexpr int kMaxBins = 128;
 
 // Each warp walks whole k_z rows; along a row |m|^2 grows with k_z, so equal bins are contiguous
-// runs of lanes.  The lowest lane of a run adds the run's values in lane order into the warp's
-// own histogram; warps and blocks are then summed in index order: a fixed reduction order.
+// runs of lanes.  A segmented scan in a fixed shuffle order sums each run, whose last lane adds it
+// to the warp's own histogram; warps and blocks are then summed in index order, so the reduction
+// order is fixed and the result is bit-reproducible.
 __global__ void __launch_bounds__(kPkThreads) k_pk_bins(int n, int pc, int nc, const float2* __restrict__ dk,
                                                         const long long* __restrict__ edges_g, int nbins,
                                                         double pscale, double kfund, double* partials) {
@@ -283,7 +284,6 @@ __global__ void __launch_bounds__(kPkThreads) k_pk_bins(int n, int pc, int nc, c
   __shared__ double hp[kPkWarps][kMaxBins];
   __shared__ double hk[kPkWarps][kMaxBins];
   __shared__ long long hc[kPkWarps][kMaxBins];
-  __shared__ double stp[kPkWarps][32], stk[kPkWarps][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int i = threadIdx.x; i <= nbins; i += blockDim.x) edges[i] = edges_g[i];
   for (int i = threadIdx.x; i < kPkWarps * kMaxBins; i += blockDim.x) {
@@ -315,20 +315,26 @@ __global__ void __launch_bounds__(kPkThreads) k_pk_bins(int n, int pc, int nc, c
           kk = sqrt((double)m2) * kfund;
         }
       }
-      const unsigned grp = __match_any_sync(0xffffffffu, bin);
-      stp[warp][lane] = p;
-      stk[warp][lane] = kk;
-      __syncwarp();
-      if (bin >= 0 && lane == __ffs(grp) - 1) {
-        double sp = 0.0, sk = 0.0;
-        for (unsigned m = grp; m; m &= m - 1) {
-          const int l = __ffs(m) - 1;
-          sp += stp[warp][l];
-          sk += stk[warp][l];
+      // segmented inclusive scan over runs of equal bins (bins never decrease along a row), in a
+      // fixed shuffle order; the last lane of each run adds the run's sums to the histogram
+      long long c = bin >= 0 ? 1 : 0;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const int ob = __shfl_up_sync(0xffffffffu, bin, d);
+        const double op = __shfl_up_sync(0xffffffffu, p, d);
+        const double ok = __shfl_up_sync(0xffffffffu, kk, d);
+        const long long oc = __shfl_up_sync(0xffffffffu, c, d);
+        if (lane >= d && ob == bin) {
+          p += op;
+          kk += ok;
+          c += oc;
         }
-        hp[warp][bin] += sp;
-        hk[warp][bin] += sk;
-        hc[warp][bin] += __popc(grp);
+      }
+      const int nb_next = __shfl_down_sync(0xffffffffu, bin, 1);
+      if (bin >= 0 && (lane == 31 || nb_next != bin)) {
+        hp[warp][bin] += p;
+        hk[warp][bin] += kk;
+        hc[warp][bin] += c;
       }
       __syncwarp();
     }
