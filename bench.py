@@ -216,6 +216,60 @@ def recorded_traffic(stage: str, workload: str):
     return ent.get("dram_bytes_per_launch_" + workload)
 
 
+def measure_adjoint(args, torch, device):
+    """Adjoint cost against the plain forward on the differentiable workload (400 Mpc/h, 128^3
+    particles, 256^3 mesh, seed 4, loss on a 64^3 CIC grid against the seed-5 realisation).
+    forward = cola_run without P(k); backward = loss-grid adjoint + cola_adjoint (10 force
+    recomputations from the per-step checkpoints).  The working set (about 0.9 GB) exceeds L2."""
+    from paper_1507_05329_gb300 import Context, Params
+    wl = cola_inputs.WORKLOADS["adjoint"]
+    cfg = cola_inputs.ADJOINT_LOSS
+    p = Params(box=wl["box"], np_side=wl["np_side"], nmesh=wl["nmesh"], nstep=10)
+    stream = torch.cuda.current_stream()
+    ctx = Context(p, stream)
+    ng = cfg["ngrid"]
+    wn = cola_inputs.white_noise_torch(p.np_side, wl["seed"], device)
+    tgt = ctx.grid_density(ctx.run(cola_inputs.white_noise_torch(p.np_side, cfg["target_seed"], device),
+                                   with_pk=False)["s"], ng)
+    out = {k: ctx.empty_particles() for k in ("s", "v", "psi1", "psi2")}
+
+    def timed(fn, k):
+        for _ in range(max(args.warmup, 3)):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / k
+
+    k = max(args.steps, 3)
+    fwd_ms = timed(lambda: ctx.run(wn, with_pk=False, out=out), k)
+    state = {}
+
+    def fwd_ckpt():
+        state["f"] = ctx.run_checkpointed(wn)
+        state["d"] = ctx.grid_density(state["f"]["s"], ng)
+
+    ck_ms = timed(fwd_ckpt, k)
+    lam_d = (2.0 * (state["d"] - tgt)).contiguous()
+
+    def backward():
+        lam_s = ctx.grid_density_adjoint(state["f"]["s"], ng, lam_d)
+        state["g"] = ctx.adjoint(wn, state["f"]["ckpt"], lam_s)
+
+    bwd_ms = timed(backward, k)
+    ctx.sync()
+    ctx.close()
+    return {"workload": f"{p.np_side}^3 particles, {p.nmesh}^3 PM mesh, L={p.box:g} Mpc/h, 10 COLA steps, "
+                        f"loss on a {ng}^3 CIC grid, seeds {wl['seed']}/{cfg['target_seed']}",
+            "forward_ms": fwd_ms, "forward_checkpointed_ms": ck_ms, "backward_ms": bwd_ms,
+            "adjoint_over_forward": bwd_ms / fwd_ms,
+            "forward_plus_backward_over_forward": (ck_ms + bwd_ms) / fwd_ms, "steps": k}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -329,6 +383,9 @@ def run_ours(args):
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_entry()
+    adj = None
+    if rank == 0 and not args.no_adjoint:
+        adj = measure_adjoint(args, torch, f"cuda:{local}")
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -337,7 +394,7 @@ def run_ours(args):
                            "l2": "inputs larger than L2 (no flush needed)",
                            "pm_step_ms": pm_ms / 10.0, "nbins": args.nbins},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clocks, "stages": per_stage}
+                "clocks": clocks, "stages": per_stage, "adjoint": adj}
         print(json.dumps(line), flush=True)
     ctx.close()
     if ws > 1:
@@ -355,6 +412,7 @@ def main():
     ap.add_argument("--nbins", type=int, default=64)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward cost measurement")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

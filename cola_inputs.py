@@ -26,6 +26,11 @@ WORKLOADS = {
 }
 
 
+# loss of the differentiable workload: CIC grid of the final density, target realisation, and the
+# central finite-difference check (step, number of directions, largest |m| of a direction)
+ADJOINT_LOSS = dict(ngrid=64, target_seed=5, fd_eps=1e-3, fd_modes=32, fd_mmax=6)
+
+
 def batched_workload():
     """The 64 uneven realisations of the batched-mock workload as a list of dicts."""
     out = []
@@ -62,3 +67,20 @@ def white_noise_torch(np_side: int, seed: int, device):
     g = torch.Generator(device=device)
     g.manual_seed(seed)
     return torch.randn(np_side ** 3, generator=g, device=device, dtype=torch.float32)
+
+
+def plane_wave_directions(np_side: int, count: int, seed: int, mmax: int) -> np.ndarray:
+    """float32 [count, np^3] real plane waves cos(2 pi m.q / np + phase) of unit amplitude per
+    lattice site (the white noise's own per-site scale), m a random nonzero integer vector with
+    |m_i| <= mmax, phase uniform in [0, 2 pi)."""
+    rng = np.random.default_rng(seed)
+    q = np.arange(np_side, dtype=np.float64)
+    qx, qy, qz = np.meshgrid(q, q, q, indexing="ij")
+    out = np.empty((count, np_side ** 3), dtype=np.float32)
+    for i in range(count):
+        m = np.zeros(3, dtype=np.int64)
+        while not m.any():
+            m = rng.integers(-mmax, mmax + 1, size=3)
+        ph = rng.uniform(0.0, 2.0 * np.pi)
+        out[i] = np.cos(2.0 * np.pi * (m[0] * qx + m[1] * qy + m[2] * qz) / np_side + ph).ravel()
+    return out

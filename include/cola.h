@@ -131,18 +131,130 @@ int cola_run(cola_ctx* ctx, const float* white_noise, float* s, float* v, float*
  * than the previous one synchronises the stream once to upload the new bin edges. */
 int cola_power_spectrum(cola_ctx* ctx, const float* s, double* pk, int nbins);
 
+/* ---- Execution schedule and autotuner (not part of the method: choices among kernels that
+ * compute the same result; every schedule gives a bit-identical density mesh and the same forces
+ * to FP32 rounding order) ---------------------------------------------------------------------
+ * Bits of a schedule:
+ *   COLA_SCHED_BINNED_DEPOSIT : particles binned into mesh tiles each step, tile-wise deposit in
+ *                               shared memory (else one global 64-bit atomic per CIC corner).
+ *                               Available when the tile geometry fits (cola_create decides).
+ *   COLA_SCHED_TILE_GATHER    : tile-wise gather from shared memory (requires the binned deposit).
+ *   COLA_SCHED_PIPELINED_FFT  : persistent cp.async-pipelined strided FFT passes (else one CTA per
+ *                               tile of pencils).
+ *   bits COLA_SCHED_BUDGET_SHIFT..+1 : shared-memory budget per CTA of the pipelined passes,
+ *                               0: 160 KB, 1: 96 KB, 2: 64 KB (sets their tile width); must be 0
+ *                               without COLA_SCHED_PIPELINED_FFT.
+ * cola_create picks a schedule from the sizes; cola_get_schedule reads it and cola_set_schedule
+ * replaces it (COLA_ERR_INVALID for an unavailable or malformed schedule).
+ * cola_autotune times `reps` PM force evaluations (deposit, FFTs, Poisson + gradient, gather) at
+ * displacements s (device float32 [3][np^3]; an evolved state is representative, a lattice is not)
+ * for every valid schedule, keeps the fastest and writes it to *best (may be NULL), and the
+ * per-candidate milliseconds, in increasing schedule order, to ms[0..max_candidates) (may be NULL).
+ * Returns the number of candidates, or minus a cola_status.  It synchronises the stream and
+ * allocates a temporary force array: call it outside graph capture. */
+#define COLA_SCHED_BINNED_DEPOSIT 1
+#define COLA_SCHED_TILE_GATHER 2
+#define COLA_SCHED_PIPELINED_FFT 4
+#define COLA_SCHED_BUDGET_SHIFT 8
+int cola_get_schedule(cola_ctx* ctx, int* schedule);
+int cola_set_schedule(cola_ctx* ctx, int schedule);
+int cola_autotune(cola_ctx* ctx, const float* s, int reps, int* best, double* ms, int max_candidates);
+
+/* ---- Reverse mode (not in the paper: the transpose of its forward model) ------------------
+ * The forward being differentiated is cola_run's: 2LPT (§2.1, §2.3), then n_step COLA steps
+ * (§2.2, eqs. cola-kick / cola-drift) with the PM force of §2.2/§2.3.  The adjoint treats the CIC
+ * weights as the continuous piecewise-linear functions of position that the 14-bit fixed-point
+ * weights approximate (their exact derivative is zero almost everywhere); the derivative of a
+ * weight is +-1 times the other two axes' weights, taken in the cell the forward's fixed-point
+ * coordinate selects.  Linear k-space maps are transposed as y -> irfft(conj(M) rfft(y)), valid for
+ * the Hermitian multipliers used here.  Float atomics sum the adjoint deposit, so adjoints agree
+ * with the exact transpose to FP32 rounding but are not bit-reproducible. */
+
+/* cola_run without P(k), storing the positions at which each step evaluates its force.
+ *   ckpt : device float32 [nstep][3][np^3], 16-byte aligned (12 nstep np^3 bytes, caller-owned);
+ *          ckpt[i-1] receives s at a_i before step i.
+ * Other arguments and results as cola_run.  Asynchronous on the context's stream. */
+int cola_run_checkpointed(cola_ctx* ctx, const float* white_noise, float* s, float* v, float* psi1, float* psi2,
+                          float* ckpt);
+
+/* Vector-Jacobian product of cola_run_checkpointed with respect to the white noise.
+ *   white_noise : the same device float32 [np^3] input as the forward (the 2LPT Hessians are
+ *                 recomputed from it).
+ *   ckpt        : the forward's checkpoints; the PM force of each step is recomputed from them.
+ *   lam_s       : cotangent of the final s, device float32 [3][np^3] (required).
+ *   lam_v, lam_psi1, lam_psi2 : cotangents of the final v_res, Psi1 and Psi2 (device float32
+ *                 [3][np^3]); NULL means zero.
+ *   lam_wn      : out, dL/d(white noise), device float32 [np^3].
+ * Inputs are not modified.  The first call allocates the adjoint work space (60 np^3 bytes plus
+ * three complex meshes, 24 nmesh^2 (nmesh/2+1) bytes); it lives until cola_destroy.  The 2LPT part
+ * reuses the context's mesh arena, so the context's meshes are undefined afterwards.
+ * All pointers 16-byte aligned; COLA_ERR_INVALID for a NULL or misaligned required pointer. */
+int cola_adjoint(cola_ctx* ctx, const float* white_noise, const float* ckpt, const float* lam_s, const float* lam_v,
+                 const float* lam_psi1, const float* lam_psi2, float* lam_wn);
+
+/* Density contrast of the particles on an ngrid^3 CIC grid covering the box (the differentiable
+ * loss's field): grid coordinate y = (q + s) ngrid / nmesh with continuous CIC weights rounded to
+ * multiples of 2^-32 and summed exactly in 64-bit integers (bit-reproducible),
+ * delta = ngrid^3 rho / np^3 - 1.
+ *   s     : device float32 [3][np^3] displacements (mesh cells).
+ *   delta : out, device float32 [ngrid][ngrid][ngrid] (row-major, z fastest).
+ * 1 <= ngrid <= nmesh.  Uses the context's density mesh as scratch. */
+int cola_grid_density(cola_ctx* ctx, const float* s, int ngrid, float* delta);
+
+/* Transpose of cola_grid_density at s: lam_s = d(sum_g lam_delta_g delta_g)/ds, with the
+ * continuous-weight derivative (one-sided at cell faces).  lam_s is overwritten. */
+int cola_grid_density_adjoint(cola_ctx* ctx, const float* s, int ngrid, const float* lam_delta, float* lam_s);
+
+/* ---- Batched realisations in one CUDA graph (the paper's many mock catalogues, §3) ----------
+ * A batch owns one context per realisation and `nstreams` non-blocking lanes.  Realisations are
+ * assigned to lanes longest-first (cost ~ particles + mesh cells x log N) and run back to back on
+ * their lane; lanes run concurrently.  cola_batch_run enqueues cola_run (2LPT + n_step PM steps +
+ * P(k) in nbins bins) of every realisation, forked from and joined back into `stream`:
+ *   use_graph = 0 : plain launches;
+ *   use_graph = 1 : the first call runs once eagerly (warm-up, then synchronises), captures the
+ *                   whole launch sequence into a CUDA graph and launches it; later calls only
+ *                   launch the graph (one host call for all realisations).
+ * io[i] holds realisation i's device buffers (as for cola_run: white noise [np^3], s, v, psi1,
+ * psi2 [3][np^3] float32, pk double [3][nbins]); all 16-byte aligned, caller-owned, fixed for the
+ * batch's lifetime (the graph records the pointers).  params[i] is realisation i's parameters
+ * (sizes may differ).  Contexts hold their own meshes: the batch needs the sum of the members'
+ * context memory.  All calls are asynchronous on `stream` except create, sync and tune.
+ * cola_batch_sync waits for `stream` and returns the first member's error flag (as cola_sync).
+ * cola_batch_tune runs cola_autotune once per distinct (np, nmesh) on that member's current s
+ * (run the batch first, so positions are evolved), gives the winner to every member of that
+ * shape and drops the captured graph (the next graph run captures again).
+ * cola_batch_info reports member i's lane and schedule and the captured graph's node count
+ * (0 before capture); any output pointer may be NULL. */
+typedef struct cola_batch cola_batch;
+typedef struct {
+  const float* white_noise;
+  float* s;
+  float* v;
+  float* psi1;
+  float* psi2;
+  double* pk;
+} cola_batch_io;
+int cola_batch_create(const cola_params* params, const cola_batch_io* io, int count, int nbins, int nstreams,
+                      void* stream, cola_batch** out);
+int cola_batch_run(cola_batch* batch, int use_graph);
+int cola_batch_sync(cola_batch* batch);
+int cola_batch_tune(cola_batch* batch, int reps);
+int cola_batch_info(cola_batch* batch, int i, int* lane, int* schedule, size_t* graph_nodes);
+void cola_batch_destroy(cola_batch* batch);
+
 /* Stage timing and launch counting (not part of the method: measurement support).
  * Stages: 0 deposit, 1 forward z (R2C), 2 forward y, 3 x + Green + gradient + inverse x,
  * 4 inverse y, 5 inverse z (C2R), 6 gather + kick + drift (or force gather), 7 x passes outside
  * the fused stage 3 (P(k), density spectrum, 2LPT), 8 2LPT element-wise kernels, 9 P(k) binning,
  * 10 mesh clearing (memset, direct deposit only), 11 spatial binning of the particles (count, scan,
- * scatter).  Stages 1, 2, 4 and 5 also count the 2LPT transforms.
+ * scatter), 12 reverse-mode and loss-grid kernels (adjoint element-wise maps, adjoint scatter and
+ * gather, loss-grid deposit).  Stages 1, 2, 4, 5 and 7 also count the 2LPT and adjoint transforms.
  * cola_profile_enable(ctx, 1) resets the totals and brackets every later launch with CUDA events
  * on the context's stream; 0 stops timing (launches are always counted).  cola_profile_read
  * synchronises the stream and writes per-stage total milliseconds and launch counts for the first
- * nstages stages (either pointer may be NULL).  Returns the number of stages (12), or minus a
+ * nstages stages (either pointer may be NULL).  Returns the number of stages (13), or minus a
  * cola_status on failure. */
-#define COLA_NUM_STAGES 12
+#define COLA_NUM_STAGES 13
 int cola_profile_enable(cola_ctx* ctx, int on);
 int cola_profile_read(cola_ctx* ctx, double* ms, long long* launches, int nstages);
 

@@ -5,4 +5,4 @@ marshals torch tensors into it.  Importing the package does not load the library
 call that needs it does, and raises if it is missing.
 """
 
-from .binding import ColaError, Context, Params, load_library, step_scalars  # noqa: F401
+from .binding import Batch, ColaError, Context, Params, load_library, step_scalars  # noqa: F401

@@ -75,10 +75,32 @@ SIGNATURES = {
     "cola_profile_enable": ([_VP, _I], _I),
     "cola_profile_read": ([_VP, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong), _I], _I),
     "cola_power_spectrum_noalloc": ([ctypes.POINTER(CParams), _VP, _VP, _I, _VP], _I),
+    "cola_run_checkpointed": ([_VP, _VP, _VP, _VP, _VP, _VP, _VP], _I),
+    "cola_adjoint": ([_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP], _I),
+    "cola_grid_density": ([_VP, _VP, _I, _VP], _I),
+    "cola_grid_density_adjoint": ([_VP, _VP, _I, _VP, _VP], _I),
+    "cola_get_schedule": ([_VP, ctypes.POINTER(_I)], _I),
+    "cola_set_schedule": ([_VP, _I], _I),
+    "cola_autotune": ([_VP, _VP, _I, ctypes.POINTER(_I), ctypes.POINTER(_D), _I], _I),
+    "cola_batch_create": ([ctypes.POINTER(CParams), _VP, _I, _I, _I, _VP, ctypes.POINTER(_VP)], _I),
+    "cola_batch_run": ([_VP, _I], _I),
+    "cola_batch_sync": ([_VP], _I),
+    "cola_batch_tune": ([_VP, _I], _I),
+    "cola_batch_info": ([_VP, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_size_t)], _I),
+    "cola_batch_destroy": ([_VP], None),
 }
 
+SCHED_BINNED_DEPOSIT = 1
+SCHED_TILE_GATHER = 2
+SCHED_PIPELINED_FFT = 4
+SCHED_BUDGET_SHIFT = 8
+
+
+class BatchIO(ctypes.Structure):
+    _fields_ = [("white_noise", _VP), ("s", _VP), ("v", _VP), ("psi1", _VP), ("psi2", _VP), ("pk", _VP)]
+
 STAGES = ["deposit", "fwd_z_r2c", "fwd_y", "green_x", "inv_y", "inv_z_c2r", "gather_kick_drift", "x_pass",
-          "ic_elementwise", "pk_bins", "clear", "bin"]
+          "ic_elementwise", "pk_bins", "clear", "bin", "adjoint"]
 
 
 def load_library(path: str = LIB_PATH):
@@ -240,3 +262,123 @@ class Context:
                                  self._particles(p2), _ptr(pk, self.torch) if with_pk else None, int(nbins)),
                "cola_run")
         return dict(s=s, v=v, psi1=p1, psi2=p2, pk=pk)
+
+    # -- reverse mode ----------------------------------------------------------------------
+    def run_checkpointed(self, white_noise):
+        """cola_run_checkpointed: returns dict(s, v, psi1, psi2, ckpt) with ckpt [nstep, 3, n]."""
+        wn = _ptr(white_noise, self.torch, (self.p.n,), self.torch.float32)
+        s, v, p1, p2 = (self.empty_particles() for _ in range(4))
+        ck = self.torch.empty((self.p.nstep, 3, self.p.n), dtype=self.torch.float32, device=self.device)
+        _check(self.lib.cola_run_checkpointed(self._ptr, wn, self._particles(s), self._particles(v),
+                                              self._particles(p1), self._particles(p2), _ptr(ck, self.torch)),
+               "cola_run_checkpointed")
+        return dict(s=s, v=v, psi1=p1, psi2=p2, ckpt=ck)
+
+    def adjoint(self, white_noise, ckpt, lam_s, lam_v=None, lam_psi1=None, lam_psi2=None):
+        """cola_adjoint: dL/d(white noise) [n] from the cotangents of the final s (and optionally
+        v_res, Psi1, Psi2)."""
+        wn = _ptr(white_noise, self.torch, (self.p.n,), self.torch.float32)
+        ck = _ptr(ckpt, self.torch, (self.p.nstep, 3, self.p.n), self.torch.float32)
+        opt = [None if t is None else self._particles(t) for t in (lam_v, lam_psi1, lam_psi2)]
+        out = self.torch.empty((self.p.n,), dtype=self.torch.float32, device=self.device)
+        _check(self.lib.cola_adjoint(self._ptr, wn, ck, self._particles(lam_s), *opt, _ptr(out, self.torch)),
+               "cola_adjoint")
+        return out
+
+    def grid_density(self, s, ngrid: int):
+        """cola_grid_density: CIC density contrast [ngrid, ngrid, ngrid] of the particles."""
+        d = self.torch.empty((ngrid, ngrid, ngrid), dtype=self.torch.float32, device=self.device)
+        _check(self.lib.cola_grid_density(self._ptr, self._particles(s), int(ngrid), _ptr(d, self.torch)),
+               "cola_grid_density")
+        return d
+
+    def grid_density_adjoint(self, s, ngrid: int, lam_delta):
+        """cola_grid_density_adjoint: d(sum lam_delta delta)/ds [3, n]."""
+        ld = _ptr(lam_delta, self.torch, (ngrid, ngrid, ngrid), self.torch.float32)
+        out = self.empty_particles()
+        _check(self.lib.cola_grid_density_adjoint(self._ptr, self._particles(s), int(ngrid), ld,
+                                                  self._particles(out)), "cola_grid_density_adjoint")
+        return out
+
+    # -- execution schedule ----------------------------------------------------------------
+    @property
+    def schedule(self) -> int:
+        out = ctypes.c_int()
+        _check(self.lib.cola_get_schedule(self._ptr, ctypes.byref(out)), "cola_get_schedule")
+        return out.value
+
+    @schedule.setter
+    def schedule(self, value: int):
+        _check(self.lib.cola_set_schedule(self._ptr, int(value)), "cola_set_schedule")
+
+    def autotune(self, s, reps: int = 3):
+        """cola_autotune at displacements s: returns (best schedule, {schedule: ms})."""
+        best = ctypes.c_int()
+        ms = (ctypes.c_double * 64)()
+        r = self.lib.cola_autotune(self._ptr, self._particles(s), int(reps), ctypes.byref(best), ms, 64)
+        if r < 0:
+            raise ColaError(-r, "cola_autotune")
+        cands = [sc for sc in range(4 << SCHED_BUDGET_SHIFT) if self._schedule_ok(sc)]
+        return best.value, {sc: ms[i] for i, sc in enumerate(cands[:r])}
+
+    def _schedule_ok(self, sc: int) -> bool:
+        keep = self.schedule
+        ok = self.lib.cola_set_schedule(self._ptr, sc) == 0
+        self.lib.cola_set_schedule(self._ptr, keep)
+        return ok
+
+
+class Batch:
+    """Many realisations run as one launch sequence over `nstreams` lanes, optionally replayed from
+    one CUDA graph (cola_batch_*).  Buffers are allocated here (torch) and fixed for the batch's
+    lifetime; results are read from ``outputs[i]``."""
+
+    def __init__(self, params: list, white_noise: list, nbins: int = 64, nstreams: int = 8, stream=None):
+        import torch
+        self.torch = torch
+        self.lib = load_library()
+        self.params = list(params)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        dev = self.stream.device
+        self.outputs = []
+        ios = (BatchIO * len(params))()
+        cps = (CParams * len(params))()
+        for i, (p, wn) in enumerate(zip(params, white_noise)):
+            _ptr(wn, torch, (p.n,), torch.float32)
+            o = {k: torch.empty((3, p.n), dtype=torch.float32, device=dev) for k in ("s", "v", "psi1", "psi2")}
+            o["pk"] = torch.empty((3, nbins), dtype=torch.float64, device=dev)
+            o["white_noise"] = wn
+            self.outputs.append(o)
+            ios[i] = BatchIO(wn.data_ptr(), o["s"].data_ptr(), o["v"].data_ptr(), o["psi1"].data_ptr(),
+                             o["psi2"].data_ptr(), o["pk"].data_ptr())
+            cps[i] = p.to_c()
+        self._ptr = ctypes.c_void_p()
+        _check(self.lib.cola_batch_create(cps, ios, len(params), int(nbins), int(nstreams),
+                                          ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(self._ptr)),
+               "cola_batch_create")
+
+    def run(self, use_graph: bool = True):
+        _check(self.lib.cola_batch_run(self._ptr, 1 if use_graph else 0), "cola_batch_run")
+
+    def sync(self):
+        _check(self.lib.cola_batch_sync(self._ptr), "cola_batch_sync")
+
+    def tune(self, reps: int = 3):
+        _check(self.lib.cola_batch_tune(self._ptr, int(reps)), "cola_batch_tune")
+
+    def info(self, i: int) -> dict:
+        lane, sched, nodes = ctypes.c_int(), ctypes.c_int(), ctypes.c_size_t()
+        _check(self.lib.cola_batch_info(self._ptr, int(i), ctypes.byref(lane), ctypes.byref(sched),
+                                        ctypes.byref(nodes)), "cola_batch_info")
+        return dict(lane=lane.value, schedule=sched.value, graph_nodes=nodes.value)
+
+    def close(self):
+        if self._ptr:
+            self.lib.cola_batch_destroy(self._ptr)
+            self._ptr = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

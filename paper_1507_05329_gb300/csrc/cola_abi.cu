@@ -76,7 +76,7 @@ void bin_edges(int nmesh, int nbins, long long* e) {
 
 enum Stage {
   kStDeposit = 0, kStFwdZ = 1, kStFwdY = 2, kStGreenX = 3, kStInvY = 4, kStInvZ = 5, kStGather = 6,
-  kStFwdX = 7, kStIc = 8, kStPk = 9, kStClear = 10, kStBin = 11
+  kStFwdX = 7, kStIc = 8, kStPk = 9, kStClear = 10, kStBin = 11, kStAdjoint = 12
 };
 
 cudaEvent_t take_event(cola_ctx* c) {
@@ -211,7 +211,8 @@ extern "C" void cola_destroy(cola_ctx* c) {
   if (c->edges_host) cudaFreeHost(c->edges_host);
   fft_plan_free(&c->mplan);
   fft_plan_free(&c->lplan);
-  void* bufs[] = {c->arena, c->dtab, c->amp_m2, c->edges, c->pk_partials, c->flags, c->mass_acc, c->bin_mem};
+  void* bufs[] = {c->arena,    c->dtab,     c->amp_m2,  c->edges, c->pk_partials,
+                  c->flags,    c->mass_acc, c->bin_mem, c->adj_mem};
   for (void* b : bufs)
     if (b) cudaFree(b);
   delete c;
@@ -454,6 +455,252 @@ extern "C" int cola_run(cola_ctx* c, const float* wn, float* s, float* v, float*
   for (int i = 1; i <= c->p.nstep; ++i) COLA_TRY(cola_step(c, i, s, v, psi1, psi2));
   if (pk) COLA_TRY(cola_power_spectrum(c, s, pk, nbins));
   return COLA_OK;
+}
+
+// ---- execution schedule and autotuner ---------------------------------------------------------
+namespace {
+constexpr int kPipeBudgetsKb[3] = {160, 96, 64};
+
+int schedule_of(const cola_ctx* c) {
+  int k = 0;
+  while (k < 2 && kPipeBudgetsKb[k] != c->mplan.pipe_kb) ++k;
+  return (c->binned ? COLA_SCHED_BINNED_DEPOSIT : 0) | (c->tile_gather ? COLA_SCHED_TILE_GATHER : 0) |
+         (c->mplan.pipe ? COLA_SCHED_PIPELINED_FFT : 0) | (k << COLA_SCHED_BUDGET_SHIFT);
+}
+
+bool schedule_valid(const cola_ctx* c, int sc) {
+  if (sc & ~(COLA_SCHED_BINNED_DEPOSIT | COLA_SCHED_TILE_GATHER | COLA_SCHED_PIPELINED_FFT |
+             (3 << COLA_SCHED_BUDGET_SHIFT)))
+    return false;
+  if ((sc & COLA_SCHED_BINNED_DEPOSIT) && !c->bin_mem) return false;
+  if ((sc & COLA_SCHED_TILE_GATHER) && !(sc & COLA_SCHED_BINNED_DEPOSIT)) return false;
+  if (((sc >> COLA_SCHED_BUDGET_SHIFT) & 3) > 2) return false;
+  if (!(sc & COLA_SCHED_PIPELINED_FFT) && ((sc >> COLA_SCHED_BUDGET_SHIFT) & 3)) return false;   // unused knob
+  return true;
+}
+
+void apply_schedule(cola_ctx* c, int sc) {
+  c->binned = (sc & COLA_SCHED_BINNED_DEPOSIT) != 0;
+  c->tile_gather = (sc & COLA_SCHED_TILE_GATHER) != 0;
+  c->mplan.pipe = (sc & COLA_SCHED_PIPELINED_FFT) != 0;
+  c->mplan.pipe_kb = kPipeBudgetsKb[(sc >> COLA_SCHED_BUDGET_SHIFT) & 3];
+}
+}  // namespace
+
+extern "C" int cola_get_schedule(cola_ctx* c, int* schedule) {
+  if (!c || !schedule) return COLA_ERR_INVALID;
+  *schedule = schedule_of(c);
+  return COLA_OK;
+}
+
+extern "C" int cola_set_schedule(cola_ctx* c, int schedule) {
+  if (!c || !schedule_valid(c, schedule)) return COLA_ERR_INVALID;
+  apply_schedule(c, schedule);
+  return COLA_OK;
+}
+
+extern "C" int cola_autotune(cola_ctx* c, const float* s, int reps, int* best, double* ms, int max_candidates) {
+  if (!c || reps < 1 || max_candidates < 0) return -COLA_ERR_INVALID;
+  if (check_ptr(s) != COLA_OK) return -COLA_ERR_INVALID;
+  std::vector<int> cand;
+  for (int sc = 0; sc < (4 << COLA_SCHED_BUDGET_SHIFT); ++sc)
+    if (schedule_valid(c, sc)) cand.push_back(sc);
+  const int keep = schedule_of(c);
+  float* force = nullptr;
+  if (cuda_status(cudaMalloc(&force, (size_t)3 * c->pg.npart * sizeof(float)), "cudaMalloc tune") != COLA_OK)
+    return -COLA_ERR_OOM;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const bool prof = c->prof;
+  c->prof = false;
+  const double fs = 1.5 * c->p.omega_m;   // force at a = 1
+  int st = COLA_OK, arg = -1;
+  float tbest = 0.0f;
+  for (size_t i = 0; i < cand.size() && st == COLA_OK; ++i) {
+    apply_schedule(c, cand[i]);
+    st = force_mesh(c, s, fs);   // warm-up (lazy kernel attributes, caches)
+    if (st == COLA_OK) st = gather(c, s, force, nullptr, nullptr, nullptr, nullptr, nullptr);
+    cudaEventRecord(e0, c->stream);
+    for (int r = 0; r < reps && st == COLA_OK; ++r) {
+      st = force_mesh(c, s, fs);
+      if (st == COLA_OK) st = gather(c, s, force, nullptr, nullptr, nullptr, nullptr, nullptr);
+    }
+    cudaEventRecord(e1, c->stream);
+    if (st == COLA_OK) st = cuda_status(cudaEventSynchronize(e1), "tune");
+    float t = 0.0f;
+    if (st == COLA_OK) cudaEventElapsedTime(&t, e0, e1);
+    t /= reps;
+    if ((int)i < max_candidates && ms) ms[i] = t;
+    if (st == COLA_OK && (arg < 0 || t < tbest)) {
+      arg = (int)i;
+      tbest = t;
+    }
+  }
+  c->prof = prof;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(force);
+  if (st != COLA_OK) {
+    apply_schedule(c, keep);
+    return -st;
+  }
+  apply_schedule(c, cand[arg]);
+  if (best) *best = cand[arg];
+  return (int)cand.size();
+}
+
+// ---- reverse mode ---------------------------------------------------------------------------
+namespace {
+
+// Adjoint work space: lam_s, lam_v, lam_Psi1, lam_Psi2, lam_F ([3][n] each) and three mesh spectra.
+int adjoint_workspace(cola_ctx* c) {
+  if (c->adj_mem) return COLA_OK;
+  const size_t pbytes = align256((size_t)3 * c->pg.npart * sizeof(float));
+  const size_t cbytes = align256(c->mesh.complex_elems() * sizeof(float2));
+  void* mem = nullptr;
+  COLA_TRY(cuda_status(cudaMalloc(&mem, 5 * pbytes + 3 * cbytes), "cudaMalloc adjoint"));
+  c->adj_mem = mem;
+  char* q = static_cast<char*>(mem);
+  for (int i = 0; i < 5; ++i) c->lam[i] = reinterpret_cast<float*>(q + i * pbytes);
+  for (int j = 0; j < 3; ++j) c->adj_mesh[j] = reinterpret_cast<float2*>(q + 5 * pbytes + j * cbytes);
+  return COLA_OK;
+}
+
+int copy_or_zero(cola_ctx* c, float* dst, const float* src, size_t bytes) {
+  if (src) return cuda_status(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, c->stream), "copy");
+  return cuda_status(cudaMemsetAsync(dst, 0, bytes, c->stream), "memset");
+}
+
+// Reverse pass of PM step i at checkpoint s_i: lam_s += d(lam_F . F(s_i))/ds_i.
+int pm_force_adjoint(cola_ctx* c, const float* s_i, double force_scale) {
+  const Grid3& g = c->mesh;
+  COLA_TRY(force_mesh(c, s_i, force_scale));   // F on the mesh, cbuf[0..2]
+  COLA_TRY(STAGED(kStClear, cuda_status(cudaMemsetAsync(c->adj_mesh[0], 0,
+                                                        3 * align256(g.complex_elems() * sizeof(float2)), c->stream),
+                                        "memset")));
+  float* const m[3] = {reinterpret_cast<float*>(c->adj_mesh[0]), reinterpret_cast<float*>(c->adj_mesh[1]),
+                       reinterpret_cast<float*>(c->adj_mesh[2])};
+  COLA_TRY(STAGED(kStAdjoint, launch_adj_deposit(c->pg, s_i, c->lam[4], m, 2LL * g.pc, c->stream)));
+  for (int j = 0; j < 3; ++j) {
+    COLA_TRY(STAGED(kStFwdZ, launch_r2c_rows(c->mplan, g, kSrcFloat, c->adj_mesh[j], 2LL * g.pc, 1.0f, c->adj_mesh[j],
+                                             c->stream)));
+    COLA_TRY(forward3d_yx(c, g, c->mplan, c->adj_mesh[j]));
+  }
+  const double kf = 2.0 * M_PI / g.n;
+  const double n3 = (double)g.n * g.n * g.n;
+  COLA_TRY(STAGED(kStAdjoint, launch_adj_combine(g, c->adj_mesh, c->dtab, (float)(force_scale / (kf * kf * n3)),
+                                                 c->adj_mesh[0], c->stream)));
+  COLA_TRY(inverse3d(c, g, c->mplan, c->adj_mesh[0]));
+  const float* f[3] = {reinterpret_cast<float*>(c->cbuf[0]), reinterpret_cast<float*>(c->cbuf[1]),
+                       reinterpret_cast<float*>(c->cbuf[2])};
+  return STAGED(kStAdjoint, launch_adj_gather(c->pg, s_i, c->lam[4], f, m[0], 2LL * g.pc,
+                                              (float)(n3 / (double)c->pg.npart), c->lam[0], c->stream));
+}
+
+// Transpose of the 2LPT maps white noise -> (Psi1, Psi2) at lam_Psi1 = lam[2], lam_Psi2 = lam[3].
+int lpt_adjoint(cola_ctx* c, const float* wn, float* lam_wn) {
+  const Grid3& g = c->lat;
+  const FftPlan& P = c->lplan;
+  const size_t lbytes = align256(g.complex_elems() * sizeof(float2));
+  float2* B[8];
+  for (int i = 0; i < 8; ++i) B[i] = reinterpret_cast<float2*>(static_cast<char*>(c->arena) + i * lbytes);
+  const long long n = c->pg.npart;
+  const float r = (float)c->p.nmesh / (float)c->p.np;
+  const float inv_n3 = (float)(1.0 / ((double)g.n * g.n * g.n));
+  // delta_L(k) / np^3 as in the forward
+  COLA_TRY(STAGED(kStFwdZ, launch_r2c_rows(P, g, kSrcFloat, wn, g.n, 1.0f, B[0], c->stream)));
+  COLA_TRY(forward3d_yx(c, g, P, B[0]));
+  COLA_TRY(STAGED(kStIc, launch_ic_amplitude(g, B[0], c->amp_m2, c->stream)));
+  // lam_S = sum_j (transpose of Psi2_j = -i kodd_j / k^2 S) lam_Psi2_j
+  for (int j = 0; j < 3; ++j) {
+    COLA_TRY(STAGED(kStAdjoint, launch_particles_to_field(g, c->lam[3] + j * n, r, B[1], c->stream)));
+    COLA_TRY(STAGED(kStFwdZ, launch_r2c_rows(P, g, kSrcFloat, B[1], 2LL * g.pc, 1.0f, B[1], c->stream)));
+    COLA_TRY(forward3d_yx(c, g, P, B[1]));
+    COLA_TRY(STAGED(kStIc, launch_ic_multiply(g, B[1], B[7], kIcPsi1, j, 0, inv_n3, c->stream, j > 0)));
+  }
+  COLA_TRY(inverse3d(c, g, P, B[7]));
+  // the six Hessians, then lam_h = lam_S dS/dh in place
+  const int pairs[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
+  for (int h = 0; h < 6; ++h) {
+    COLA_TRY(STAGED(kStIc, launch_ic_multiply(g, B[0], B[1 + h], kIcHess, pairs[h][0], pairs[h][1], 1.0f, c->stream)));
+    COLA_TRY(inverse3d(c, g, P, B[1 + h]));
+  }
+  float2* const hs[6] = {B[1], B[2], B[3], B[4], B[5], B[6]};
+  COLA_TRY(STAGED(kStAdjoint, launch_ic_source_adjoint(g, B[7], hs, c->stream)));
+  // acc(k) = sum_h H_h F(lam_h) + sum_j (i kodd_j / k^2)^* r F(lam_Psi1_j); lam_w = inverse(amp acc)
+  for (int h = 0; h < 6; ++h) {
+    COLA_TRY(STAGED(kStFwdZ, launch_r2c_rows(P, g, kSrcFloat, B[1 + h], 2LL * g.pc, 1.0f, B[1 + h], c->stream)));
+    COLA_TRY(forward3d_yx(c, g, P, B[1 + h]));
+    COLA_TRY(STAGED(kStIc, launch_ic_multiply(g, B[1 + h], B[0], kIcHess, pairs[h][0], pairs[h][1], 1.0f, c->stream,
+                                              h > 0)));
+  }
+  for (int j = 0; j < 3; ++j) {
+    COLA_TRY(STAGED(kStAdjoint, launch_particles_to_field(g, c->lam[2] + j * n, r, B[7], c->stream)));
+    COLA_TRY(STAGED(kStFwdZ, launch_r2c_rows(P, g, kSrcFloat, B[7], 2LL * g.pc, 1.0f, B[7], c->stream)));
+    COLA_TRY(forward3d_yx(c, g, P, B[7]));
+    COLA_TRY(STAGED(kStIc, launch_ic_multiply(g, B[7], B[0], kIcPsi2, j, 0, 1.0f, c->stream, true)));
+  }
+  COLA_TRY(STAGED(kStIc, launch_ic_amplitude(g, B[0], c->amp_m2, c->stream)));
+  COLA_TRY(inverse3d(c, g, P, B[0]));
+  return STAGED(kStIc, launch_ic_to_particles(g, B[0], 1.0f, lam_wn, c->stream));
+}
+
+}  // namespace
+
+extern "C" int cola_run_checkpointed(cola_ctx* c, const float* wn, float* s, float* v, float* psi1, float* psi2,
+                                     float* ckpt) {
+  if (!c) return COLA_ERR_INVALID;
+  COLA_TRY(check_ptr(ckpt));
+  const size_t pbytes = (size_t)3 * c->pg.npart * sizeof(float);
+  COLA_TRY(cola_ic_2lpt(c, wn, s, v, psi1, psi2));
+  for (int i = 1; i <= c->p.nstep; ++i) {
+    COLA_TRY(cuda_status(cudaMemcpyAsync(reinterpret_cast<char*>(ckpt) + (i - 1) * pbytes, s, pbytes,
+                                         cudaMemcpyDeviceToDevice, c->stream), "checkpoint"));
+    COLA_TRY(cola_step(c, i, s, v, psi1, psi2));
+  }
+  return COLA_OK;
+}
+
+extern "C" int cola_adjoint(cola_ctx* c, const float* wn, const float* ckpt, const float* lam_s, const float* lam_v,
+                            const float* lam_psi1, const float* lam_psi2, float* lam_wn) {
+  if (!c) return COLA_ERR_INVALID;
+  for (const void* p : {(const void*)wn, (const void*)ckpt, (const void*)lam_s, (const void*)lam_wn})
+    COLA_TRY(check_ptr(p));
+  for (const void* p : {(const void*)lam_v, (const void*)lam_psi1, (const void*)lam_psi2})
+    if (p) COLA_TRY(check_ptr(p));
+  COLA_TRY(adjoint_workspace(c));
+  const long long n = c->pg.npart;
+  const size_t pbytes = (size_t)3 * n * sizeof(float);
+  COLA_TRY(copy_or_zero(c, c->lam[0], lam_s, pbytes));
+  COLA_TRY(copy_or_zero(c, c->lam[1], lam_v, pbytes));
+  COLA_TRY(copy_or_zero(c, c->lam[2], lam_psi1, pbytes));
+  COLA_TRY(copy_or_zero(c, c->lam[3], lam_psi2, pbytes));
+  for (int i = c->p.nstep; i >= 1; --i) {
+    const StepScalars& ss = c->steps[i];
+    COLA_TRY(STAGED(kStAdjoint, launch_adj_step(3 * n, c->lam[0], c->lam[1], c->lam[2], c->lam[3], c->lam[4], ss,
+                                                c->stream)));
+    const float* s_i = reinterpret_cast<const float*>(reinterpret_cast<const char*>(ckpt) + (i - 1) * pbytes);
+    COLA_TRY(pm_force_adjoint(c, s_i, ss.force_scale));
+  }
+  const StepScalars& s0 = c->steps[0];
+  COLA_TRY(STAGED(kStAdjoint, launch_adj_ic(3 * n, c->lam[0], c->lam[2], c->lam[3], (float)s0.d1, (float)s0.d2,
+                                            c->stream)));
+  return lpt_adjoint(c, wn, lam_wn);
+}
+
+extern "C" int cola_grid_density(cola_ctx* c, const float* s, int ngrid, float* delta) {
+  if (!c || ngrid < 1 || ngrid > c->mesh.n) return COLA_ERR_INVALID;
+  COLA_TRY(check_ptr(s));
+  COLA_TRY(check_ptr(delta));
+  return STAGED(kStAdjoint, launch_grid_density(c->pg, s, ngrid, c->rho, delta, c->stream));
+}
+
+extern "C" int cola_grid_density_adjoint(cola_ctx* c, const float* s, int ngrid, const float* lam_delta,
+                                         float* lam_s) {
+  if (!c || ngrid < 1 || ngrid > c->mesh.n) return COLA_ERR_INVALID;
+  for (const void* p : {(const void*)s, (const void*)lam_delta, (const void*)lam_s}) COLA_TRY(check_ptr(p));
+  return STAGED(kStAdjoint, launch_grid_density_adjoint(c->pg, s, ngrid, lam_delta, lam_s, c->stream));
 }
 
 extern "C" int cola_profile_enable(cola_ctx* c, int on) {

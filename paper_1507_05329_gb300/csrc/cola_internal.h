@@ -52,6 +52,10 @@ struct FftPlan {
   int w_pencil = 8;       // pencils per CTA in the strided passes
   int w_rows = 4;         // row pairs per CTA in the contiguous (R2C / C2R) passes
   int ept = 16;           // complex elements per thread
+  // schedule (chosen by cola_set_schedule / cola_autotune): persistent pipelined strided passes
+  // on/off, and their shared-memory budget per CTA (sets the tile width)
+  bool pipe = true;
+  int pipe_kb = 160;
 };
 
 // Factor n into radices {16, 8, 5, 4, 3, 2}; returns false if n has another prime factor.
@@ -159,12 +163,29 @@ int launch_gather_tiles(const ParticleGeom& pg, const BinGeom& b, const BinBuffe
 enum IcField { kIcPsi1 = 0, kIcHess = 1, kIcPsi2 = 2 };
 int launch_ic_amplitude(const Grid3& g, float2* wk, const float* amp_m2, cudaStream_t st);
 int launch_ic_multiply(const Grid3& g, const float2* src, float2* dst, IcField kind, int i, int j,
-                       float scale, cudaStream_t st);
+                       float scale, cudaStream_t st, bool accumulate = false);
 int launch_ic_source(const Grid3& g, float2* const h[6], float2* dst, cudaStream_t st);
 int launch_ic_to_particles(const Grid3& g, const float2* field, float scale, float* dst,
                            cudaStream_t st);
 int launch_ic_positions(long long npart, const float* psi1, const float* psi2, float d1, float d2,
                         float* s, float* v, cudaStream_t st);
+
+// Adjoint (adjoint.cu).
+int launch_adj_step(long long n3, const float* lam_s, float* lam_v, float* lam_p1, float* lam_p2, float* lam_f,
+                    const StepScalars& sc, cudaStream_t st);
+int launch_adj_deposit(const ParticleGeom& pg, const float* s, const float* lam_f, float* const m[3], long long rs,
+                       cudaStream_t st);
+int launch_adj_combine(const Grid3& g, float2* const l[3], const float* dtab, float g_scale, float2* out,
+                       cudaStream_t st);
+int launch_adj_gather(const ParticleGeom& pg, const float* s, const float* lam_f, const float* const f[3],
+                      const float* lam_delta, long long rs, float norm, float* lam_s, cudaStream_t st);
+int launch_adj_ic(long long n3, const float* lam_s, float* lam_p1, float* lam_p2, float d1, float d2, cudaStream_t st);
+int launch_particles_to_field(const Grid3& g, const float* src, float scale, float2* dst, cudaStream_t st);
+int launch_ic_source_adjoint(const Grid3& g, const float2* lam_src, float2* const h[6], cudaStream_t st);
+int launch_grid_density(const ParticleGeom& pg, const float* s, int ngrid, unsigned long long* scratch, float* delta,
+                        cudaStream_t st);
+int launch_grid_density_adjoint(const ParticleGeom& pg, const float* s, int ngrid, const float* lam_delta,
+                                float* lam_s, cudaStream_t st);
 
 // Power spectrum binning of a forward spectrum (side n).
 int launch_pk_bins(const Grid3& g, const float2* dk, const long long* edges, int nbins,
@@ -209,4 +230,8 @@ struct cola_ctx {
   struct Mark { int stage; cudaEvent_t a, b; };
   std::vector<Mark> marks;
   std::vector<cudaEvent_t> event_pool;
+  // adjoint work space (allocated by the first cola_adjoint call)
+  void* adj_mem = nullptr;
+  float* lam[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // lam_s, lam_v, lam_psi1, lam_psi2, lam_F
+  float2* adj_mesh[3] = {nullptr, nullptr, nullptr};
 };

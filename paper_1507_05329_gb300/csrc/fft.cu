@@ -39,10 +39,12 @@ struct PipeShape {
   size_t smem;
 };
 
-PipeShape pipe_shape(const Grid3& g) {
+PipeShape pipe_shape(const Grid3& g, int budget_kb) {
   PipeShape ps;
   int lw = 1;   // W >= 2: 16-byte copies
-  while ((2 << lw) <= largest_pow2_le(g.nc) && (size_t)3 * (g.n + g.n / 16 + 1) * (2 << lw) * 8 <= 160 * 1024) ++lw;
+  while ((2 << lw) <= largest_pow2_le(g.nc) &&
+         (size_t)3 * (g.n + g.n / 16 + 1) * (2 << lw) * 8 <= (size_t)budget_kb * 1024)
+    ++lw;
   ps.lw = lw;
   ps.smem = (size_t)3 * (g.n + g.n / 16 + 1) * (1 << lw) * sizeof(float2);
   int th = ((g.n << lw) + kPipeEpt - 1) / kPipeEpt;
@@ -58,9 +60,9 @@ PipeShape pipe_shape(const Grid3& g) {
 }
 
 // The pipelined kernels need at least two columns per tile and a whole tile per thread set.
-bool pipe_ok(const Grid3& g) {
-  if (g.nc < 2) return false;
-  const PipeShape ps = pipe_shape(g);
+bool pipe_ok(const FftPlan& p, const Grid3& g) {
+  if (!p.pipe || g.nc < 2) return false;
+  const PipeShape ps = pipe_shape(g, p.pipe_kb);
   return (long long)ps.threads * kPipeEpt >= (long long)(g.n << ps.lw) && ps.smem <= 200 * 1024;
 }
 
@@ -205,8 +207,8 @@ int launch_pencils(const FftPlan& p, const Grid3& g, int axis, int dir, float2* 
   const long long jstride = axis == 1 ? g.pc : plane;
   const long long ostride = axis == 1 ? plane : g.pc;
   FastPlan fp;
-  if (fast_plan(p, &fp) && pipe_ok(g)) {
-    const PipeShape ps = pipe_shape(g);
+  if (fast_plan(p, &fp) && pipe_ok(p, g)) {
+    const PipeShape ps = pipe_shape(g, p.pipe_kb);
     if (max_radix(fp) > 8)
       pipe_pencils_launch<16>(fp, ps.lw, ps.ctas, ps.threads, ps.smem, dir, data, jstride, ostride, g.nc, ps.nchunks,
                               ps.ntiles, st);

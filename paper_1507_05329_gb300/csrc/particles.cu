@@ -201,7 +201,7 @@ __global__ void k_ic_amplitude(int n, int pc, int nc, float2* wk, const float* _
 // uses the full k_i, off-diagonal the Nyquist-zeroed kodd); Psi2 component i: -i kodd_i / k^2.
 // k in radians per lattice spacing, times 'scale'.
 __global__ void k_ic_multiply(int n, int pc, int nc, const float2* __restrict__ src, float2* dst, int kind,
-                              int ci, int cj, float scale) {
+                              int ci, int cj, float scale, int accumulate) {
   const long long total = (long long)n * n * nc;
   const float kf = 6.283185307179586f / n;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
@@ -232,6 +232,10 @@ __global__ void k_ic_multiply(int n, int pc, int nc, const float2* __restrict__ 
         const float c = kk * inv_k2 * scale;
         out = make_float2(c * z.x, c * z.y);
       }
+    }
+    if (accumulate) {
+      const float2 o = dst[row * pc + kz];
+      out = make_float2(out.x + o.x, out.y + o.y);
     }
     dst[row * pc + kz] = out;
   }
@@ -426,9 +430,9 @@ int launch_ic_amplitude(const Grid3& g, float2* wk, const float* amp_m2, cudaStr
 }
 
 int launch_ic_multiply(const Grid3& g, const float2* src, float2* dst, IcField kind, int i, int j, float scale,
-                       cudaStream_t st) {
+                       cudaStream_t st, bool accumulate) {
   k_ic_multiply<<<grid_for((long long)g.rows() * g.nc, 256), 256, 0, st>>>(g.n, g.pc, g.nc, src, dst, (int)kind,
-                                                                           i, j, scale);
+                                                                           i, j, scale, accumulate ? 1 : 0);
   return check_launch("ic_multiply");
 }
 
