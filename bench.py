@@ -270,6 +270,74 @@ def measure_adjoint(args, torch, device):
             "forward_plus_backward_over_forward": (ck_ms + bwd_ms) / fwd_ms, "steps": k}
 
 
+def measure_batched(args, torch, device):
+    """Batched mocks: the 64 uneven realisations (24 x 96^3/192^3/300, 24 x 128^3/256^3/400,
+    16 x 160^3/320^3/500 Mpc/h, seeds 100-163, 10 COLA steps and P(k) each).  Plain = one
+    realisation after another through cola_run on one stream; batched = cola_batch over
+    `--lanes` streams, autotuned per shape, replayed from one captured CUDA graph.  The working
+    set (about 30 GB) exceeds L2."""
+    from paper_1507_05329_gb300 import Batch, Context, Params
+    members = cola_inputs.batched_workload()
+    params = [Params(box=m["box"], np_side=m["np_side"], nmesh=m["nmesh"], nstep=10) for m in members]
+    wns = [cola_inputs.white_noise_torch(p.np_side, m["seed"], device) for p, m in zip(params, members)]
+    stream = torch.cuda.current_stream()
+    k = max(args.steps, 2)
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    # plain: one context per shape, realisations in sequence
+    ctxs = {}
+    for p in params:
+        if (p.np_side, p.nmesh, p.box) not in ctxs:
+            ctxs[(p.np_side, p.nmesh, p.box)] = Context(p, stream)
+    outs = {key: {n: c.empty_particles() for n in ("s", "v", "psi1", "psi2")} for key, c in ctxs.items()}
+    for key, o in outs.items():
+        o["pk"] = torch.empty((3, 64), dtype=torch.float64, device=device)
+
+    def plain():
+        for p, w in zip(params, wns):
+            key = (p.np_side, p.nmesh, p.box)
+            ctxs[key].run(w, 64, out=outs[key])
+
+    plain_ms = timed(plain, k)
+    for c in ctxs.values():
+        c.sync()
+        c.close()
+    del ctxs, outs
+    torch.cuda.empty_cache()
+
+    batch = Batch(params, wns, nbins=64, nstreams=args.lanes, stream=stream)
+    batch.run(use_graph=False)
+    batch.sync()
+    batch.tune(reps=2)
+    batch.run(use_graph=True)   # warm-up + capture + launch
+    batch.sync()
+    graph_ms = timed(lambda: batch.run(use_graph=True), k)
+    eager_ms = timed(lambda: batch.run(use_graph=False), k)
+    batch.sync()
+    info = [batch.info(i) for i in range(len(params))]
+    scheds = {}
+    for p, inf in zip(params, info):
+        scheds[f"{p.np_side}^3/{p.nmesh}^3"] = inf["schedule"]
+    batch.close()
+    n = len(params)
+    return {"workload": "64 realisations: 24 x (96^3, 192^3, 300 Mpc/h), 24 x (128^3, 256^3, 400), "
+                        "16 x (160^3, 320^3, 500), seeds 100-163, 10 COLA steps + P(k) each",
+            "mocks_per_hour": n * 3.6e6 / graph_ms, "graph_ms_per_batch": graph_ms,
+            "plain_mocks_per_hour": n * 3.6e6 / plain_ms, "plain_ms_per_batch": plain_ms,
+            "eager_lanes_ms_per_batch": eager_ms, "speedup_vs_plain": plain_ms / graph_ms,
+            "lanes": args.lanes, "graph_nodes": info[0]["graph_nodes"], "schedules": scheds, "steps": k}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -380,12 +448,17 @@ def run_ours(args):
         del wn_host, s_host, v_host, pk_host
 
     ctx.sync()
+    ctx.close()
+    del out, wn
+    torch.cuda.empty_cache()
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_entry()
-    adj = None
+    adj = batched = None
     if rank == 0 and not args.no_adjoint:
         adj = measure_adjoint(args, torch, f"cuda:{local}")
+    if rank == 0 and not args.no_batched:
+        batched = measure_batched(args, torch, f"cuda:{local}")
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -394,9 +467,8 @@ def run_ours(args):
                            "l2": "inputs larger than L2 (no flush needed)",
                            "pm_step_ms": pm_ms / 10.0, "nbins": args.nbins},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clocks, "stages": per_stage, "adjoint": adj}
+                "clocks": clocks, "stages": per_stage, "adjoint": adj, "batched": batched}
         print(json.dumps(line), flush=True)
-    ctx.close()
     if ws > 1:
         dist.destroy_process_group()
     return 0
@@ -413,6 +485,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward cost measurement")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-mocks measurement")
+    ap.add_argument("--lanes", type=int, default=8, help="streams of the batched-mocks run")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

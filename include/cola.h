@@ -138,7 +138,8 @@ int cola_power_spectrum(cola_ctx* ctx, const float* s, double* pk, int nbins);
  *   COLA_SCHED_BINNED_DEPOSIT : particles binned into mesh tiles each step, tile-wise deposit in
  *                               shared memory (else one global 64-bit atomic per CIC corner).
  *                               Available when the tile geometry fits (cola_create decides).
- *   COLA_SCHED_TILE_GATHER    : tile-wise gather from shared memory (requires the binned deposit).
+ *   COLA_SCHED_TILE_GATHER    : tile-wise gather from shared memory (requires the binned deposit
+ *                               and tiles of at least 4 cells along z).
  *   COLA_SCHED_PIPELINED_FFT  : persistent cp.async-pipelined strided FFT passes (else one CTA per
  *                               tile of pencils).
  *   bits COLA_SCHED_BUDGET_SHIFT..+1 : shared-memory budget per CTA of the pipelined passes,
@@ -241,6 +242,37 @@ int cola_batch_sync(cola_batch* batch);
 int cola_batch_tune(cola_batch* batch, int reps);
 int cola_batch_info(cola_batch* batch, int i, int* lane, int* schedule, size_t* graph_nodes);
 void cola_batch_destroy(cola_batch* batch);
+
+/* P(k) as cola_power_spectrum, with options:
+ *   COLA_PK_CIC_CORRECT : correct each mode for the CIC smoothing and aliasing and subtract shot
+ *                         noise (the paper corrects with Jing 2005, §3.3; this is that correction for
+ *                         a locally flat spectrum): P = P_raw / C2(k) - V/n with
+ *                         C2 = prod_i (1 - (2/3) sin^2(pi m_i / N)), the CIC window squared summed
+ *                         over all aliases.  P can then be negative where the signal is below shot noise.
+ * Other flag bits give COLA_ERR_INVALID. */
+#define COLA_PK_CIC_CORRECT 1
+int cola_power_spectrum_ex(cola_ctx* ctx, const float* s, double* pk, int nbins, int flags);
+
+/* Snapshot between two force times (§2.2: the kick/drift equations interpolate the particles to
+ * output redshifts between steps).  Input: the state right after cola_step(i): s (at a_{i+1}, or at
+ * a_{n_step} = 1 after the last step), v = v_res at a_{i+1/2}, psi1, psi2.  Output at
+ * a_i <= a_snap <= a_{i+1} (a_snap = 1 after the last step):
+ *   s_out = s_i + drift(a_i -> a_snap) v_res + (D1(a_snap) - D1(a_i)) Psi1 + (D2(a_snap) - D2(a_i)) Psi2,
+ *   v_out = v_res + a^2 dD1/dt Psi1 + a^2 dD2/dt Psi2 at a_snap (canonical velocity; may be NULL),
+ * the drift integral of eq. (cola-drift) with the step's a_{i+1/2} and ansatz, evaluated up to
+ * a_snap; the residual velocity between kicks is v_res(a_{i+1/2}).  COLA_ERR_INVALID if a_snap is
+ * outside the step's interval.  s_out must not alias s. */
+int cola_snapshot(cola_ctx* ctx, int i, double a_snap, const float* s, const float* v, const float* psi1,
+                  const float* psi2, float* s_out, float* v_out);
+
+/* cola_run that also writes snapshots at nsnap increasing scale factors a_snap[k] in [a_1, 1]
+ * (the paper writes its density fields at z = 0.73, 0.6, 0.44 and 0):
+ *   s_snap : device float32 [nsnap][3][np^3] (required), v_snap : same shape or NULL,
+ *   pk_snap: device double [nsnap][3][nbins] or NULL, computed with cola_power_spectrum_ex(pk_flags).
+ * s, v, psi1, psi2 end at a = 1 as after cola_run. */
+int cola_run_snapshots(cola_ctx* ctx, const float* white_noise, float* s, float* v, float* psi1, float* psi2,
+                       const double* a_snap, int nsnap, float* s_snap, float* v_snap, double* pk_snap, int nbins,
+                       int pk_flags);
 
 /* Stage timing and launch counting (not part of the method: measurement support).
  * Stages: 0 deposit, 1 forward z (R2C), 2 forward y, 3 x + Green + gradient + inverse x,

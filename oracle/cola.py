@@ -52,6 +52,32 @@ def step(i: int, s, v, psi1, psi2, p: cosmology.Params, force=None):
     return s, v
 
 
+def snapshot(i: int, s, v, psi1, psi2, p: cosmology.Params, a_snap: float, force=None):
+    """Positions and canonical velocities at a_snap between the force times a_i and a_{i+1}
+    (§2.2: the kick/drift equations also interpolate between steps), from the state (s_i, v_res at
+    a_{i-1/2}) before step i: kick as in ``step``, then the drift of eq. (cola-drift) and the 2LPT
+    growth taken only up to a_snap.  The residual velocity between kicks is v_res(a_{i+1/2})
+    (reading 18).  a_i <= a_snap <= a_{i+1} (a_snap = a_i = 1 after the last step)."""
+    c = cosmology.step_scalars(p, i)
+    a_i = c["a"]
+    if not (a_i - 1e-12 <= a_snap <= c["a_next"] + 1e-12):
+        raise ValueError("a_snap outside [a_i, a_{i+1}]")
+    s = np.asarray(s, dtype=np.float64)
+    v = np.asarray(v, dtype=np.float64)
+    psi1 = np.asarray(psi1, dtype=np.float64)
+    psi2 = np.asarray(psi2, dtype=np.float64)
+    f = pm.pm_force(s, p.np_side, p.nmesh, c["force_scale"]) if force is None else force(s, c["force_scale"])
+    v = v + c["kick"] * (f - (c["c1"] * psi1 + c["c2"] * psi2))
+    om = p.omega_m
+    if c["drift"] == 0.0 and c["dd1"] == 0.0:   # the last step does not drift
+        drift = 0.0
+    else:
+        drift = cosmology.drift_factor(a_i, a_snap, c["a_hi"], om, p.nlpt, p.drift_ansatz)
+    s = (s + drift * v + (cosmology.d1(a_snap, om) - cosmology.d1(a_i, om)) * psi1
+         + (cosmology.d2(a_snap, om) - cosmology.d2(a_i, om)) * psi2)
+    return s, final_velocity(v, psi1, psi2, p, a_snap)
+
+
 def final_velocity(v_res, psi1, psi2, p: cosmology.Params, a: float = 1.0):
     """Canonical velocity v = v_res + a^2 dx_2LPT/dt at a (reading 15)."""
     f1, f2 = cosmology.lpt_velocity_factors(a, p.omega_m)

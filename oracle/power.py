@@ -5,7 +5,10 @@ Test infrastructure only (see ``oracle/__init__.py``).
 Paper passage: §3.3 (matter power spectrum).  CIC density on a mesh, FFT, keep the modes
 {k_z > 0} U {k_z = 0, k_y > 0} U {k_z = 0, k_y = 0, k_x > 0} of the k_z >= 0 half so that no
 mode is counted twice, P(k) = V^-1 <|delta(k)|^2> per bin, plotted against the mean |k| of the
-bin's modes.
+bin's modes.  The paper corrects the CIC smoothing and aliasing with the procedure of Jing
+(2005); ``power_spectrum(..., cic_correct=True, n_particles=n)`` applies that correction for a
+locally flat spectrum: per mode P = P_raw / C2(k) - V/n, with the alias-summed CIC window
+C2(k) = sum_n W^2(k + 2 k_N n) = prod_i (1 - (2/3) sin^2(pi m_i / N)) (reading 19).
 
 Readings: delta(k) = (V/N^3) sum_x delta_x e^{-i k.x}, so P = V |DFT|^2 / N^6.  Bins
 are log spaced between the fundamental k_f = 2 pi / L and the Nyquist k_N = pi N / L (the paper
@@ -37,12 +40,23 @@ def half_space_mask(nmesh: int) -> np.ndarray:
     return (mz > 0) | ((mz == 0) & (my > 0)) | ((mz == 0) & (my == 0) & (mx > 0))
 
 
-def power_spectrum(delta: np.ndarray, box: float, nbins: int):
+def cic_alias_sum(mx, my, mz, n: int):
+    """C2(m) = prod_i (1 - (2/3) sin^2(pi m_i / N)): the CIC window squared summed over aliases."""
+    out = 1.0
+    for m in (mx, my, mz):
+        out = out * (1.0 - (2.0 / 3.0) * np.sin(np.pi * np.asarray(m, dtype=np.float64) / n) ** 2)
+    return out
+
+
+def power_spectrum(delta: np.ndarray, box: float, nbins: int, cic_correct: bool = False,
+                   n_particles: int | None = None):
     """(k_mean [nbins], P [nbins], n_modes [nbins]) of a density contrast field delta [N, N, N]."""
     n = delta.shape[0]
     dk = fourier.rfft3(delta)
     pmode = np.abs(dk) ** 2 * (box ** 3 / float(n) ** 6)
     mx, my, mz = fourier.mode_grids(n)
+    if cic_correct:
+        pmode = pmode / cic_alias_sum(mx, my, mz, n) - box ** 3 / float(n_particles)
     m2 = mx * mx + my * my + mz * mz
     m2 = np.broadcast_to(m2, dk.shape)
     kmag = np.sqrt(m2.astype(np.float64)) * (2.0 * np.pi / box)

@@ -79,6 +79,9 @@ SIGNATURES = {
     "cola_adjoint": ([_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP], _I),
     "cola_grid_density": ([_VP, _VP, _I, _VP], _I),
     "cola_grid_density_adjoint": ([_VP, _VP, _I, _VP, _VP], _I),
+    "cola_power_spectrum_ex": ([_VP, _VP, _VP, _I, _I], _I),
+    "cola_snapshot": ([_VP, _I, _D, _VP, _VP, _VP, _VP, _VP, _VP], _I),
+    "cola_run_snapshots": ([_VP, _VP, _VP, _VP, _VP, _VP, ctypes.POINTER(_D), _I, _VP, _VP, _VP, _I, _I], _I),
     "cola_get_schedule": ([_VP, ctypes.POINTER(_I)], _I),
     "cola_set_schedule": ([_VP, _I], _I),
     "cola_autotune": ([_VP, _VP, _I, ctypes.POINTER(_I), ctypes.POINTER(_D), _I], _I),
@@ -90,6 +93,7 @@ SIGNATURES = {
     "cola_batch_destroy": ([_VP], None),
 }
 
+PK_CIC_CORRECT = 1
 SCHED_BINNED_DEPOSIT = 1
 SCHED_TILE_GATHER = 2
 SCHED_PIPELINED_FFT = 4
@@ -247,6 +251,37 @@ class Context:
         _check(self.lib.cola_power_spectrum(self._ptr, self._particles(s), _ptr(pk, self.torch), int(nbins)),
                "cola_power_spectrum")
         return pk
+
+    def power_spectrum_ex(self, s, nbins: int = 64, cic_correct: bool = False):
+        """cola_power_spectrum_ex: P(k), optionally CIC-window/alias corrected and shot-noise subtracted."""
+        pk = self.torch.empty((3, nbins), dtype=self.torch.float64, device=self.device)
+        _check(self.lib.cola_power_spectrum_ex(self._ptr, self._particles(s), _ptr(pk, self.torch), int(nbins),
+                                               PK_CIC_CORRECT if cic_correct else 0), "cola_power_spectrum_ex")
+        return pk
+
+    def snapshot(self, i: int, a_snap: float, s, v, psi1, psi2, with_velocity: bool = True):
+        """cola_snapshot after step i: returns (s at a_snap, canonical v at a_snap or None)."""
+        so = self.empty_particles()
+        vo = self.empty_particles() if with_velocity else None
+        _check(self.lib.cola_snapshot(self._ptr, int(i), float(a_snap), self._particles(s), self._particles(v),
+                                      self._particles(psi1), self._particles(psi2), self._particles(so),
+                                      self._particles(vo) if vo is not None else None), "cola_snapshot")
+        return so, vo
+
+    def run_snapshots(self, white_noise, a_snap, nbins: int = 64, with_pk: bool = True, cic_correct: bool = False):
+        """cola_run_snapshots: dict(s, v, psi1, psi2, s_snap [k,3,n], v_snap, pk_snap [k,3,nbins])."""
+        wn = _ptr(white_noise, self.torch, (self.p.n,), self.torch.float32)
+        k = len(a_snap)
+        s, v, p1, p2 = (self.empty_particles() for _ in range(4))
+        ss = self.torch.empty((k, 3, self.p.n), dtype=self.torch.float32, device=self.device)
+        vs = self.torch.empty((k, 3, self.p.n), dtype=self.torch.float32, device=self.device)
+        pk = self.torch.empty((k, 3, nbins), dtype=self.torch.float64, device=self.device) if with_pk else None
+        arr = (ctypes.c_double * k)(*[float(a) for a in a_snap])
+        _check(self.lib.cola_run_snapshots(self._ptr, wn, self._particles(s), self._particles(v),
+                                           self._particles(p1), self._particles(p2), arr, k, _ptr(ss, self.torch),
+                                           _ptr(vs, self.torch), _ptr(pk, self.torch) if with_pk else None,
+                                           int(nbins), PK_CIC_CORRECT if cic_correct else 0), "cola_run_snapshots")
+        return dict(s=s, v=v, psi1=p1, psi2=p2, s_snap=ss, v_snap=vs, pk_snap=pk)
 
     def run(self, white_noise, nbins: int = 64, with_pk: bool = True, out: dict | None = None):
         """A whole realisation (cola_run).  ``out`` may hold preallocated s, v, psi1, psi2, pk tensors."""

@@ -426,8 +426,8 @@ extern "C" int cola_step(cola_ctx* c, int i, float* s, float* v, const float* ps
   return gather(c, nullptr, nullptr, s, v, psi1, psi2, &kd);
 }
 
-extern "C" int cola_power_spectrum(cola_ctx* c, const float* s, double* pk, int nbins) {
-  if (!c || nbins < 1 || nbins > kPkMaxBins) return COLA_ERR_INVALID;
+extern "C" int cola_power_spectrum_ex(cola_ctx* c, const float* s, double* pk, int nbins, int flags) {
+  if (!c || nbins < 1 || nbins > kPkMaxBins || (flags & ~COLA_PK_CIC_CORRECT)) return COLA_ERR_INVALID;
   COLA_TRY(check_ptr(s));
   COLA_TRY(check_ptr(pk));
   if (nbins != c->edges_nbins) {
@@ -441,11 +441,41 @@ extern "C" int cola_power_spectrum(cola_ctx* c, const float* s, double* pk, int 
   COLA_TRY(deposit_and_forward_yz(c, s));
   COLA_TRY(STAGED(kStFwdX, launch_pencils(c->mplan, c->mesh, 0, -1, c->cbuf[2], c->stream)));
   const double nn = c->mesh.n;
-  const double pscale = std::pow(c->p.box, 3) / (nn * nn * nn * nn * nn * nn);
+  const double vol = std::pow(c->p.box, 3);
+  const double pscale = vol / (nn * nn * nn * nn * nn * nn);
   const double kfund = 2.0 * M_PI / c->p.box;
-  COLA_TRY(STAGED(kStPk, launch_pk_bins(c->mesh, c->cbuf[2], c->edges, nbins, pscale, kfund, c->pk_partials,
-                                        c->pk_blocks, c->stream)));
+  const int corr = (flags & COLA_PK_CIC_CORRECT) ? 1 : 0;
+  COLA_TRY(STAGED(kStPk, launch_pk_bins(c->mesh, c->cbuf[2], c->edges, nbins, pscale, kfund, corr,
+                                        vol / (double)c->pg.npart, c->pk_partials, c->pk_blocks, c->stream)));
   return STAGED(kStPk, launch_pk_finish(c->pk_partials, c->pk_blocks, nbins, pk, c->stream));
+}
+
+extern "C" int cola_power_spectrum(cola_ctx* c, const float* s, double* pk, int nbins) {
+  return cola_power_spectrum_ex(c, s, pk, nbins, 0);
+}
+
+extern "C" int cola_snapshot(cola_ctx* c, int i, double a_snap, const float* s, const float* v, const float* psi1,
+                             const float* psi2, float* s_out, float* v_out) {
+  if (!c || i < 1 || i > c->p.nstep) return COLA_ERR_INVALID;
+  for (const void* p : {(const void*)s, (const void*)v, (const void*)psi1, (const void*)psi2, (const void*)s_out})
+    COLA_TRY(check_ptr(p));
+  if (v_out) COLA_TRY(check_ptr(v_out));
+  const StepScalars& ss = c->steps[i];
+  const bool last = i == c->p.nstep;
+  const double a_next = last ? ss.a : (double)(i + 1) / c->p.nstep;
+  if (!(a_snap >= ss.a - 1e-12 && a_snap <= a_next + 1e-12)) return COLA_ERR_INVALID;
+  const Cosmo cosmo(c->p.omega_m, c->p.h, c->p.n_s, c->p.sigma8);
+  // the state holds s at a_next and v_res at a_{i+1/2}: step back from a_next to a_snap
+  double alpha = 0.0, b1 = 0.0, b2 = 0.0;
+  if (!last) {
+    alpha = -cosmo.drift(a_snap, a_next, ss.a_hi, c->p.nlpt, c->p.drift_ansatz);
+    b1 = cosmo.d1(a_snap) - cosmo.d1(a_next);
+    b2 = cosmo.d2(a_snap) - cosmo.d2(a_next);
+  }
+  const double f = a_snap * a_snap * a_snap * hubble(a_snap, c->p.omega_m);   // a^2 d/dt = a^3 H d/da
+  const double g1 = f * cosmo.d1_da(a_snap), g2 = f * cosmo.d2_da(a_snap);
+  return STAGED(kStIc, launch_snapshot(c->pg.npart, s, v, psi1, psi2, (float)alpha, (float)b1, (float)b2, (float)g1,
+                                       (float)g2, s_out, v_out, c->stream));
 }
 
 extern "C" int cola_run(cola_ctx* c, const float* wn, float* s, float* v, float* psi1, float* psi2, double* pk,
@@ -454,6 +484,30 @@ extern "C" int cola_run(cola_ctx* c, const float* wn, float* s, float* v, float*
   COLA_TRY(cola_ic_2lpt(c, wn, s, v, psi1, psi2));
   for (int i = 1; i <= c->p.nstep; ++i) COLA_TRY(cola_step(c, i, s, v, psi1, psi2));
   if (pk) COLA_TRY(cola_power_spectrum(c, s, pk, nbins));
+  return COLA_OK;
+}
+
+extern "C" int cola_run_snapshots(cola_ctx* c, const float* wn, float* s, float* v, float* psi1, float* psi2,
+                                  const double* a_snap, int nsnap, float* s_snap, float* v_snap, double* pk_snap,
+                                  int nbins, int pk_flags) {
+  if (!c || nsnap < 1 || !a_snap || !s_snap) return COLA_ERR_INVALID;
+  const double a1 = 1.0 / c->p.nstep;
+  for (int k = 0; k < nsnap; ++k)
+    if (!(a_snap[k] >= a1 && a_snap[k] <= 1.0 + 1e-12) || (k > 0 && !(a_snap[k] > a_snap[k - 1])))
+      return COLA_ERR_INVALID;
+  const size_t pbytes = (size_t)3 * c->pg.npart * sizeof(float);
+  COLA_TRY(cola_ic_2lpt(c, wn, s, v, psi1, psi2));
+  int k = 0;
+  for (int i = 1; i <= c->p.nstep; ++i) {
+    COLA_TRY(cola_step(c, i, s, v, psi1, psi2));
+    const double a_next = i == c->p.nstep ? 1.0 : (double)(i + 1) / c->p.nstep;
+    for (; k < nsnap && a_snap[k] <= a_next + 1e-12; ++k) {
+      float* so = reinterpret_cast<float*>(reinterpret_cast<char*>(s_snap) + k * pbytes);
+      float* vo = v_snap ? reinterpret_cast<float*>(reinterpret_cast<char*>(v_snap) + k * pbytes) : nullptr;
+      COLA_TRY(cola_snapshot(c, i, a_snap[k], s, v, psi1, psi2, so, vo));
+      if (pk_snap) COLA_TRY(cola_power_spectrum_ex(c, so, pk_snap + (size_t)k * 3 * nbins, nbins, pk_flags));
+    }
+  }
   return COLA_OK;
 }
 
@@ -474,6 +528,7 @@ bool schedule_valid(const cola_ctx* c, int sc) {
     return false;
   if ((sc & COLA_SCHED_BINNED_DEPOSIT) && !c->bin_mem) return false;
   if ((sc & COLA_SCHED_TILE_GATHER) && !(sc & COLA_SCHED_BINNED_DEPOSIT)) return false;
+  if ((sc & COLA_SCHED_TILE_GATHER) && c->bg.lz < 2) return false;   // 16-byte staging copies along z
   if (((sc >> COLA_SCHED_BUDGET_SHIFT) & 3) > 2) return false;
   if (!(sc & COLA_SCHED_PIPELINED_FFT) && ((sc >> COLA_SCHED_BUDGET_SHIFT) & 3)) return false;   // unused knob
   return true;

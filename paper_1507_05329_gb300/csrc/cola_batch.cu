@@ -36,7 +36,9 @@ double realisation_cost(const cola_params& p) {
 struct cola_batch {
   int count = 0;
   int nbins = 0;
-  cudaStream_t main = nullptr;
+  cudaStream_t main = nullptr;          // the caller's stream (may be the legacy default stream)
+  cudaStream_t origin = nullptr;        // owned: capture origin and graph launch stream
+  cudaEvent_t start = nullptr, done = nullptr;
   std::vector<cudaStream_t> streams;    // owned
   std::vector<int> lane;                // member -> stream index
   std::vector<cola_ctx*> ctx;           // owned
@@ -50,9 +52,9 @@ struct cola_batch {
 
 namespace {
 
-// Enqueue every member on its lane, the lanes forked from and joined back into b->main.
-int enqueue(cola_batch* b) {
-  BATCH_TRY(cuda_status(cudaEventRecord(b->fork, b->main), "fork"));
+// Enqueue every member on its lane, the lanes forked from and joined back into `on`.
+int enqueue(cola_batch* b, cudaStream_t on) {
+  BATCH_TRY(cuda_status(cudaEventRecord(b->fork, on), "fork"));
   for (cudaStream_t s : b->streams) BATCH_TRY(cuda_status(cudaStreamWaitEvent(s, b->fork, 0), "fork wait"));
   for (int i = 0; i < b->count; ++i) {
     const cola_batch_io& o = b->io[i];
@@ -60,7 +62,7 @@ int enqueue(cola_batch* b) {
   }
   for (size_t l = 0; l < b->streams.size(); ++l) {
     BATCH_TRY(cuda_status(cudaEventRecord(b->join[l], b->streams[l]), "join"));
-    BATCH_TRY(cuda_status(cudaStreamWaitEvent(b->main, b->join[l], 0), "join wait"));
+    BATCH_TRY(cuda_status(cudaStreamWaitEvent(on, b->join[l], 0), "join wait"));
   }
   return COLA_OK;
 }
@@ -77,12 +79,16 @@ void drop_graph(cola_batch* b) {
 extern "C" void cola_batch_destroy(cola_batch* b) {
   if (!b) return;
   if (b->main) cudaStreamSynchronize(b->main);
+  if (b->origin) cudaStreamSynchronize(b->origin);
   for (cudaStream_t s : b->streams) cudaStreamSynchronize(s);
   drop_graph(b);
   for (cola_ctx* c : b->ctx) cola_destroy(c);
   for (cudaStream_t s : b->streams) cudaStreamDestroy(s);
   for (cudaEvent_t e : b->join) cudaEventDestroy(e);
   if (b->fork) cudaEventDestroy(b->fork);
+  if (b->start) cudaEventDestroy(b->start);
+  if (b->done) cudaEventDestroy(b->done);
+  if (b->origin) cudaStreamDestroy(b->origin);
   delete b;
 }
 
@@ -116,6 +122,9 @@ extern "C" int cola_batch_create(const cola_params* params, const cola_batch_io*
     if (st == COLA_OK) st = cuda_status(cudaEventCreateWithFlags(&b->join[l], cudaEventDisableTiming), "event");
   }
   if (st == COLA_OK) st = cuda_status(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming), "event");
+  if (st == COLA_OK) st = cuda_status(cudaEventCreateWithFlags(&b->start, cudaEventDisableTiming), "event");
+  if (st == COLA_OK) st = cuda_status(cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming), "event");
+  if (st == COLA_OK) st = cuda_status(cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking), "stream");
   if (st != COLA_OK) return fail(st);
   // longest-processing-time-first: the costliest realisation goes to the least loaded lane
   std::vector<int> order(count);
@@ -141,7 +150,7 @@ extern "C" int cola_batch_run(cola_batch* b, int use_graph) {
   if (!b) return COLA_ERR_INVALID;
   if (!use_graph || !b->warmed) {
     // eager: also the warm-up before a capture (first-use kernel attributes, P(k) bin edges)
-    BATCH_TRY(enqueue(b));
+    BATCH_TRY(enqueue(b, b->main));
     if (use_graph) {
       BATCH_TRY(cuda_status(cudaStreamSynchronize(b->main), "warm-up"));
       b->warmed = true;
@@ -149,10 +158,11 @@ extern "C" int cola_batch_run(cola_batch* b, int use_graph) {
     if (!use_graph) return COLA_OK;
   }
   if (!b->exec) {
-    BATCH_TRY(cuda_status(cudaStreamBeginCapture(b->main, cudaStreamCaptureModeRelaxed), "begin capture"));
-    const int st = enqueue(b);
+    // capture on the batch's own stream (the caller's may be the uncapturable legacy stream)
+    BATCH_TRY(cuda_status(cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeRelaxed), "begin capture"));
+    const int st = enqueue(b, b->origin);
     cudaGraph_t g = nullptr;
-    const int st2 = cuda_status(cudaStreamEndCapture(b->main, &g), "end capture");
+    const int st2 = cuda_status(cudaStreamEndCapture(b->origin, &g), "end capture");
     if (st != COLA_OK || st2 != COLA_OK) {
       if (g) cudaGraphDestroy(g);
       return st != COLA_OK ? st : st2;
@@ -163,7 +173,12 @@ extern "C" int cola_batch_run(cola_batch* b, int use_graph) {
       return COLA_ERR_CUDA;
     }
   }
-  return cuda_status(cudaGraphLaunch(b->exec, b->main), "graph launch");
+  // order the replay after the caller's stream and the caller's stream after the replay
+  BATCH_TRY(cuda_status(cudaEventRecord(b->start, b->main), "start"));
+  BATCH_TRY(cuda_status(cudaStreamWaitEvent(b->origin, b->start, 0), "start wait"));
+  BATCH_TRY(cuda_status(cudaGraphLaunch(b->exec, b->origin), "graph launch"));
+  BATCH_TRY(cuda_status(cudaEventRecord(b->done, b->origin), "done"));
+  return cuda_status(cudaStreamWaitEvent(b->main, b->done, 0), "done wait");
 }
 
 extern "C" int cola_batch_sync(cola_batch* b) {

@@ -187,9 +187,14 @@ int launch_grid_density(const ParticleGeom& pg, const float* s, int ngrid, unsig
 int launch_grid_density_adjoint(const ParticleGeom& pg, const float* s, int ngrid, const float* lam_delta,
                                 float* lam_s, cudaStream_t st);
 
+// Snapshot between force times: s_out = s + alpha v + b1 psi1 + b2 psi2; v_out = v + g1 psi1 + g2 psi2
+// (v_out may be null).
+int launch_snapshot(long long npart, const float* s, const float* v, const float* psi1, const float* psi2, float alpha,
+                    float b1, float b2, float g1, float g2, float* s_out, float* v_out, cudaStream_t st);
+
 // Power spectrum binning of a forward spectrum (side n).
-int launch_pk_bins(const Grid3& g, const float2* dk, const long long* edges, int nbins,
-                   double pscale, double kfund, double* partials, int nblocks, cudaStream_t st);
+int launch_pk_bins(const Grid3& g, const float2* dk, const long long* edges, int nbins, double pscale, double kfund,
+                   int cic_correct, double shot, double* partials, int nblocks, cudaStream_t st);
 int launch_pk_finish(const double* partials, int nblocks, int nbins, double* pk, cudaStream_t st);
 int launch_dense_spectrum(const Grid3& g, const float2* src, float* dst, cudaStream_t st);
 

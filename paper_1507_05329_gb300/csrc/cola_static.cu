@@ -142,7 +142,7 @@ extern "C" int cola_power_spectrum_noalloc(const cola_params* p, const float* s,
   if (r == COLA_OK) r = launch_pencils(plan, g, 1, -1, spec, st);
   if (r == COLA_OK) r = launch_pencils(plan, g, 0, -1, spec, st);
   const double pscale = std::pow(p->box, 3) / std::pow((double)n, 6);
-  if (r == COLA_OK) r = launch_pk_bins(g, spec, edg, nbins, pscale, 2.0 * M_PI / p->box, part, kBlocks, st);
+  if (r == COLA_OK) r = launch_pk_bins(g, spec, edg, nbins, pscale, 2.0 * M_PI / p->box, 0, 0.0, part, kBlocks, st);
   if (r == COLA_OK) r = launch_pk_finish(part, kBlocks, nbins, pk, st);
   return r;
 }

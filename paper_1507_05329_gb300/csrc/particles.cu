@@ -272,6 +272,18 @@ __global__ void k_ic_positions(long long n3, const float* __restrict__ psi1, con
   }
 }
 
+// s_out = s + alpha v + b1 psi1 + b2 psi2;  v_out = v + g1 psi1 + g2 psi2   (all [3][n])
+__global__ void k_snapshot(long long n3, const float* __restrict__ s, const float* __restrict__ v,
+                           const float* __restrict__ psi1, const float* __restrict__ psi2, float alpha, float b1,
+                           float b2, float g1, float g2, float* s_out, float* v_out) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n3;
+       t += (long long)gridDim.x * blockDim.x) {
+    const float p1 = psi1[t], p2 = psi2[t], vv = v[t];
+    s_out[t] = s[t] + alpha * vv + b1 * p1 + b2 * p2;
+    if (v_out) v_out[t] = vv + g1 * p1 + g2 * p2;
+  }
+}
+
 // ---- power spectrum ------------------------------------------------------------------------
 constexpr int kPkThreads = 256;
 constexpr int kPkWarps = kPkThreads / 32;
@@ -281,9 +293,12 @@ constexpr int kMaxBins = 128;
 // runs of lanes.  A segmented scan in a fixed shuffle order sums each run, whose last lane adds it
 // to the warp's own histogram; warps and blocks are then summed in index order, so the reduction
 // order is fixed and the result is bit-reproducible.
+// cic_correct: per mode P / C2(m) - shot, C2 = prod_i (1 - (2/3) sin^2(pi m_i / n)) the CIC window
+// squared summed over its aliases (Jing 2005 for a locally flat spectrum), shot = V / particles.
 __global__ void __launch_bounds__(kPkThreads) k_pk_bins(int n, int pc, int nc, const float2* __restrict__ dk,
                                                         const long long* __restrict__ edges_g, int nbins,
-                                                        double pscale, double kfund, double* partials) {
+                                                        double pscale, double kfund, int cic_correct, double shot,
+                                                        double* partials) {
   __shared__ long long edges[kMaxBins + 1];
   __shared__ double hp[kPkWarps][kMaxBins];
   __shared__ double hk[kPkWarps][kMaxBins];
@@ -316,6 +331,12 @@ __global__ void __launch_bounds__(kPkThreads) k_pk_bins(int n, int pc, int nc, c
           bin = lo;
           const float2 z = dk[row * pc + kz];
           p = ((double)z.x * z.x + (double)z.y * z.y) * pscale;
+          if (cic_correct) {
+            const double sx = sin(M_PI * mx / n), sy = sin(M_PI * my / n), sz = sin(M_PI * kz / n);
+            const double c2 = (1.0 - (2.0 / 3.0) * sx * sx) * (1.0 - (2.0 / 3.0) * sy * sy) *
+                              (1.0 - (2.0 / 3.0) * sz * sz);
+            p = p / c2 - shot;
+          }
           kk = sqrt((double)m2) * kfund;
         }
       }
@@ -455,9 +476,17 @@ int launch_ic_positions(long long npart, const float* psi1, const float* psi2, f
   return check_launch("ic_positions");
 }
 
-int launch_pk_bins(const Grid3& g, const float2* dk, const long long* edges, int nbins, double pscale,
-                   double kfund, double* partials, int nblocks, cudaStream_t st) {
-  k_pk_bins<<<nblocks, kPkThreads, 0, st>>>(g.n, g.pc, g.nc, dk, edges, nbins, pscale, kfund, partials);
+int launch_snapshot(long long npart, const float* s, const float* v, const float* psi1, const float* psi2, float alpha,
+                    float b1, float b2, float g1, float g2, float* s_out, float* v_out, cudaStream_t st) {
+  k_snapshot<<<grid_for(3 * npart, 256), 256, 0, st>>>(3 * npart, s, v, psi1, psi2, alpha, b1, b2, g1, g2, s_out,
+                                                       v_out);
+  return check_launch("snapshot");
+}
+
+int launch_pk_bins(const Grid3& g, const float2* dk, const long long* edges, int nbins, double pscale, double kfund,
+                   int cic_correct, double shot, double* partials, int nblocks, cudaStream_t st) {
+  k_pk_bins<<<nblocks, kPkThreads, 0, st>>>(g.n, g.pc, g.nc, dk, edges, nbins, pscale, kfund, cic_correct, shot,
+                                             partials);
   return check_launch("pk_bins");
 }
 
