@@ -40,7 +40,8 @@ typedef enum {
     COLA_ERR_OOM = 2,         /* device allocation failed */
     COLA_ERR_CUDA = 3,        /* a CUDA runtime call failed */
     COLA_ERR_OVERFLOW = 4,    /* a fixed-point mesh cell overflowed (more than 2^22 particles) */
-    COLA_ERR_NONFINITE = 5    /* a particle position or velocity became NaN or infinite */
+    COLA_ERR_NONFINITE = 5,   /* a particle position or velocity became NaN or infinite */
+    COLA_ERR_INTERNAL = 6     /* a bounded device loop hit its limit (never expected; result invalid) */
 } cola_status;
 
 /* Parameters of one realisation (§1 cosmology, §2.2 time stepping, §2.3 box and mesh).
@@ -274,19 +275,40 @@ int cola_run_snapshots(cola_ctx* ctx, const float* white_noise, float* s, float*
                        const double* a_snap, int nsnap, float* s_snap, float* v_snap, double* pk_snap, int nbins,
                        int pk_flags);
 
+/* Friends-of-friends haloes (§2.3, run on the fly by the paper; §3.2: linking length b = 0.2 times
+ * the mean particle separation, 0.37 for 2LPT).  Links are decided exactly on the deposit's
+ * fixed-point coordinates G (20 fractional bits per mesh cell): friends when the periodic
+ * minimum-image distance satisfies d^2 <= l^2 in integers, l = rint(b (nmesh/np) 2^20).  Groups are
+ * the connected components (friends of friends), labelled by their smallest particle id, so the
+ * output is unique and bit-reproducible.
+ *   s          : device float32 [3][np^3] displacements (mesh cells).
+ *   b          : linking length in mean particle separations, 0 < b, l <= 2^30.
+ *   n_min      : smallest halo (>= 1).
+ *   label, size: out, device int32 [np^3]: group label and member count of each particle.
+ *   halo_label, halo_size : out, device int32 [capacity] or NULL; halo_pos : out, device double
+ *                [3][capacity] or NULL, the periodic centre of mass in mesh cells in [0, nmesh)
+ *                (G_root + exact integer sum of minimum-image offsets / size, in FP64).  Haloes
+ *                (groups of >= n_min members) are listed in increasing label order; only the first
+ *                `capacity` are written.
+ *   nhalo      : out, device int32: the number of haloes (may exceed capacity).
+ * Work space (about 52 B per particle plus the search cells) is allocated on first use and kept
+ * until cola_destroy; requires np^3 < 2^31.  Asynchronous on the context's stream. */
+int cola_fof(cola_ctx* ctx, const float* s, double b, int n_min, int* label, int* size, int* halo_label,
+             int* halo_size, double* halo_pos, int capacity, int* nhalo);
+
 /* Stage timing and launch counting (not part of the method: measurement support).
  * Stages: 0 deposit, 1 forward z (R2C), 2 forward y, 3 x + Green + gradient + inverse x,
  * 4 inverse y, 5 inverse z (C2R), 6 gather + kick + drift (or force gather), 7 x passes outside
  * the fused stage 3 (P(k), density spectrum, 2LPT), 8 2LPT element-wise kernels, 9 P(k) binning,
  * 10 mesh clearing (memset, direct deposit only), 11 spatial binning of the particles (count, scan,
  * scatter), 12 reverse-mode and loss-grid kernels (adjoint element-wise maps, adjoint scatter and
- * gather, loss-grid deposit).  Stages 1, 2, 4, 5 and 7 also count the 2LPT and adjoint transforms.
+ * gather, loss-grid deposit), 13 friends-of-friends.  Stages 1, 2, 4, 5 and 7 also count the 2LPT and adjoint transforms.
  * cola_profile_enable(ctx, 1) resets the totals and brackets every later launch with CUDA events
  * on the context's stream; 0 stops timing (launches are always counted).  cola_profile_read
  * synchronises the stream and writes per-stage total milliseconds and launch counts for the first
- * nstages stages (either pointer may be NULL).  Returns the number of stages (13), or minus a
+ * nstages stages (either pointer may be NULL).  Returns the number of stages (14), or minus a
  * cola_status on failure. */
-#define COLA_NUM_STAGES 13
+#define COLA_NUM_STAGES 14
 int cola_profile_enable(cola_ctx* ctx, int on);
 int cola_profile_read(cola_ctx* ctx, double* ms, long long* launches, int nstages);
 

@@ -15,13 +15,15 @@ least n_min members; its position is the periodic centre of mass, computed as
 G_root + (sum of minimum-image offsets G_j - G_root) / size in FP64 from exact integer sums, then
 wrapped into [0, N) mesh cells.  Haloes are listed in increasing label order.
 
-A library primitive (scipy's connected components) serves as the component step; the pair search
-is brute force over all pairs.
+Library primitives serve as steps: scipy's connected components, and for large inputs scipy's
+periodic k-d tree as a candidate pair search (radius slightly above l, then the exact integer test
+decides), which ``tests/test_oracle_fof.py`` pins against the brute-force search over all pairs.
 """
 
 from __future__ import annotations
 
 import numpy as np
+from scipy.spatial import cKDTree
 from scipy.sparse import coo_matrix
 from scipy.sparse.csgraph import connected_components
 
@@ -59,7 +61,23 @@ def friend_pairs(g, nmesh: int, ell: int):
     return np.concatenate(ii), np.concatenate(jj)
 
 
-def fof(s, np_side: int, nmesh: int, b: float = 0.2, n_min: int = 1):
+def friend_pairs_kdtree(g, nmesh: int, ell: int):
+    """The pairs of ``friend_pairs`` from a periodic k-d tree: candidates within l (1 + 1e-9)
+    (G / 2^20 is exact in FP64), then the exact integer test."""
+    modulus = nmesh << cic.FRAC_BITS
+    x = g.T.astype(np.float64) / float(1 << cic.FRAC_BITS)
+    tree = cKDTree(x, boxsize=float(nmesh))
+    pairs = tree.query_pairs(ell / float(1 << cic.FRAC_BITS) * (1.0 + 1e-9), output_type="ndarray")
+    if pairs.size == 0:
+        return np.zeros(0, dtype=np.int64), np.zeros(0, dtype=np.int64)
+    i = np.minimum(pairs[:, 0], pairs[:, 1]).astype(np.int64)
+    j = np.maximum(pairs[:, 0], pairs[:, 1]).astype(np.int64)
+    d = _wrap(g[:, j] - g[:, i], modulus)
+    keep = np.all(np.abs(d) <= ell, axis=0) & (np.sum(d * d, axis=0) <= ell * ell)
+    return i[keep], j[keep]
+
+
+def fof(s, np_side: int, nmesh: int, b: float = 0.2, n_min: int = 1, search: str = "auto"):
     """FoF groups of the particles at displacement s [3, n] (float32 mesh cells).
 
     Returns dict(label [n] (smallest id in the group), size [n] (members of the particle's group),
@@ -69,7 +87,8 @@ def fof(s, np_side: int, nmesh: int, b: float = 0.2, n_min: int = 1):
     n = g.shape[1]
     modulus = nmesh << cic.FRAC_BITS
     ell = linking_length_fixed(b, np_side, nmesh)
-    i, j = friend_pairs(g, nmesh, ell)
+    use_tree = search == "kdtree" or (search == "auto" and n > 20000)
+    i, j = friend_pairs_kdtree(g, nmesh, ell) if use_tree else friend_pairs(g, nmesh, ell)
     graph = coo_matrix((np.ones(i.size), (i, j)), shape=(n, n))
     _, comp = connected_components(graph, directed=False)
     root = np.full(comp.max() + 1, n, dtype=np.int64)
@@ -78,12 +97,11 @@ def fof(s, np_side: int, nmesh: int, b: float = 0.2, n_min: int = 1):
     counts = np.bincount(label, minlength=n)
     size = counts[label]
     roots = np.nonzero((label == np.arange(n)) & (counts >= n_min))[0]
-    pos = np.zeros((3, roots.size))
-    for h, r in enumerate(roots):
-        members = np.nonzero(label == r)[0]
-        off = _wrap(g[:, members] - g[:, r:r + 1], modulus)
-        tot = off.sum(axis=1)                                   # exact int64 sums
-        com = g[:, r].astype(np.float64) + tot.astype(np.float64) / float(members.size)
-        com = np.mod(com, float(modulus))
-        pos[:, h] = com / float(1 << cic.FRAC_BITS)
+    # exact int64 sums of the minimum-image offsets of every member to its root
+    off = _wrap(g - g[:, label], modulus)
+    tot = np.zeros((3, n), dtype=np.int64)
+    for a in range(3):
+        np.add.at(tot[a], label, off[a])
+    com = g[:, roots].astype(np.float64) + tot[:, roots].astype(np.float64) / counts[roots].astype(np.float64)
+    pos = np.mod(com, float(modulus)) / float(1 << cic.FRAC_BITS)
     return dict(label=label, size=size, halo_label=roots, halo_size=counts[roots], halo_pos=pos)

@@ -15,7 +15,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libcola.so")
 
 STATUS = {0: "ok", 1: "invalid argument or size", 2: "device allocation failed", 3: "CUDA runtime error",
-          4: "fixed-point density overflow", 5: "non-finite particle position or velocity"}
+          4: "fixed-point density overflow", 5: "non-finite particle position or velocity",
+          6: "internal iteration limit reached"}
 
 
 class ColaError(RuntimeError):
@@ -82,6 +83,7 @@ SIGNATURES = {
     "cola_power_spectrum_ex": ([_VP, _VP, _VP, _I, _I], _I),
     "cola_snapshot": ([_VP, _I, _D, _VP, _VP, _VP, _VP, _VP, _VP], _I),
     "cola_run_snapshots": ([_VP, _VP, _VP, _VP, _VP, _VP, ctypes.POINTER(_D), _I, _VP, _VP, _VP, _I, _I], _I),
+    "cola_fof": ([_VP, _VP, _D, _I, _VP, _VP, _VP, _VP, _VP, _I, _VP], _I),
     "cola_get_schedule": ([_VP, ctypes.POINTER(_I)], _I),
     "cola_set_schedule": ([_VP, _I], _I),
     "cola_autotune": ([_VP, _VP, _I, ctypes.POINTER(_I), ctypes.POINTER(_D), _I], _I),
@@ -104,7 +106,7 @@ class BatchIO(ctypes.Structure):
     _fields_ = [("white_noise", _VP), ("s", _VP), ("v", _VP), ("psi1", _VP), ("psi2", _VP), ("pk", _VP)]
 
 STAGES = ["deposit", "fwd_z_r2c", "fwd_y", "green_x", "inv_y", "inv_z_c2r", "gather_kick_drift", "x_pass",
-          "ic_elementwise", "pk_bins", "clear", "bin", "adjoint"]
+          "ic_elementwise", "pk_bins", "clear", "bin", "adjoint", "fof"]
 
 
 def load_library(path: str = LIB_PATH):
@@ -334,6 +336,24 @@ class Context:
         _check(self.lib.cola_grid_density_adjoint(self._ptr, self._particles(s), int(ngrid), ld,
                                                   self._particles(out)), "cola_grid_density_adjoint")
         return out
+
+    # -- friends-of-friends ----------------------------------------------------------------
+    def fof(self, s, b: float = 0.2, n_min: int = 20, capacity: int | None = None):
+        """cola_fof: dict(label [n], size [n], halo_label [h], halo_size [h], halo_pos [3, h], nhalo)."""
+        t = self.torch
+        n = self.p.n
+        cap = n if capacity is None else int(capacity)
+        label = t.empty(n, dtype=t.int32, device=self.device)
+        size = t.empty(n, dtype=t.int32, device=self.device)
+        hl = t.empty(max(cap, 1), dtype=t.int32, device=self.device)
+        hs = t.empty(max(cap, 1), dtype=t.int32, device=self.device)
+        hp = t.empty((3, max(cap, 1)), dtype=t.float64, device=self.device)
+        nh = t.zeros(4, dtype=t.int32, device=self.device)
+        _check(self.lib.cola_fof(self._ptr, self._particles(s), float(b), int(n_min), _ptr(label, t), _ptr(size, t),
+                                 _ptr(hl, t), _ptr(hs, t), _ptr(hp, t), cap, _ptr(nh, t)), "cola_fof")
+        nhalo = int(nh[0])
+        k = min(nhalo, cap)
+        return dict(label=label, size=size, halo_label=hl[:k], halo_size=hs[:k], halo_pos=hp[:, :k], nhalo=nhalo)
 
     # -- execution schedule ----------------------------------------------------------------
     @property

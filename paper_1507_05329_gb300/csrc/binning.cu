@@ -453,6 +453,14 @@ bool tile_gather_pays(const BinGeom& b, long long npart) {
   return b.lz >= 2 && npart >= 384LL * groups;
 }
 
+int launch_excl_scan(const unsigned* cnt, int m, unsigned* seg, unsigned* off, unsigned* cur, cudaStream_t st) {
+  const int nseg = (m + kScanSeg - 1) / kScanSeg;
+  k_scan_sums<<<dim3(nseg, 1), kScanThreads, 0, st>>>(cnt, cnt, m, seg);
+  k_scan_segs<<<1, kScanThreads, 0, st>>>(seg, nseg);
+  k_scan_apply<<<dim3(nseg, 1), kScanThreads, 0, st>>>(cnt, cnt, m, seg, off, off, cur, cur);
+  return check_launch("excl_scan");
+}
+
 int launch_binning(const ParticleGeom& pg, const BinGeom& b, const float* s, BinBuffers& bb, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {

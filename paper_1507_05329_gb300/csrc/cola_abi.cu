@@ -76,7 +76,7 @@ void bin_edges(int nmesh, int nbins, long long* e) {
 
 enum Stage {
   kStDeposit = 0, kStFwdZ = 1, kStFwdY = 2, kStGreenX = 3, kStInvY = 4, kStInvZ = 5, kStGather = 6,
-  kStFwdX = 7, kStIc = 8, kStPk = 9, kStClear = 10, kStBin = 11, kStAdjoint = 12
+  kStFwdX = 7, kStIc = 8, kStPk = 9, kStClear = 10, kStBin = 11, kStAdjoint = 12, kStFof = 13
 };
 
 cudaEvent_t take_event(cola_ctx* c) {
@@ -177,6 +177,7 @@ extern "C" const char* cola_strerror(int status) {
     case COLA_ERR_CUDA: return "CUDA runtime error";
     case COLA_ERR_OVERFLOW: return "fixed-point density overflow";
     case COLA_ERR_NONFINITE: return "non-finite particle position or velocity";
+    case COLA_ERR_INTERNAL: return "internal iteration limit reached";
     default: return "unknown status";
   }
 }
@@ -212,7 +213,7 @@ extern "C" void cola_destroy(cola_ctx* c) {
   fft_plan_free(&c->mplan);
   fft_plan_free(&c->lplan);
   void* bufs[] = {c->arena,    c->dtab,     c->amp_m2,  c->edges, c->pk_partials,
-                  c->flags,    c->mass_acc, c->bin_mem, c->adj_mem};
+                  c->flags,    c->mass_acc, c->bin_mem, c->adj_mem,     c->fof_mem,  c->fof_sums};
   for (void* b : bufs)
     if (b) cudaFree(b);
   delete c;
@@ -344,6 +345,7 @@ extern "C" int cola_sync(cola_ctx* c) {
   if (flags) cudaMemset(c->flags, 0, sizeof(int));
   if (flags & 1) return COLA_ERR_OVERFLOW;
   if (flags & 2) return COLA_ERR_NONFINITE;
+  if (flags & 4) return COLA_ERR_INTERNAL;
   return COLA_OK;
 }
 
@@ -603,6 +605,67 @@ extern "C" int cola_autotune(cola_ctx* c, const float* s, int reps, int* best, d
   apply_schedule(c, cand[arg]);
   if (best) *best = cand[arg];
   return (int)cand.size();
+}
+
+// ---- friends-of-friends ------------------------------------------------------------------------
+namespace {
+
+int fof_workspace(cola_ctx* c, const FofGeom& f, int capacity) {
+  const long long n = c->pg.npart;
+  if (!c->fof_mem || c->fof_ncells < f.ncells) {
+    if (c->fof_mem) {
+      COLA_TRY(cuda_status(cudaStreamSynchronize(c->stream), "fof realloc"));
+      cudaFree(c->fof_mem);
+      c->fof_mem = nullptr;
+    }
+    const long long nseg = ((n > f.ncells ? n : f.ncells) + 4095) / 4096 + 1;
+    const size_t b8 = align256((size_t)n * 8), b4 = align256((size_t)(n + 1) * 4);
+    const size_t bc = align256((size_t)(f.ncells + 1) * 4);
+    const size_t bytes = 3 * b8 + 7 * b4 + 3 * bc + align256((size_t)nseg * 4);
+    void* mem = nullptr;
+    COLA_TRY(cuda_status(cudaMalloc(&mem, bytes), "cudaMalloc fof"));
+    c->fof_mem = mem;
+    c->fof_ncells = f.ncells;
+    char* q = static_cast<char*>(mem);
+    for (int a = 0; a < 3; ++a, q += b8) c->fb.g[a] = reinterpret_cast<long long*>(q);
+    int** ints[3] = {&c->fb.key, &c->fb.sorted, &c->fb.parent};
+    for (int i = 0; i < 3; ++i, q += b4) *ints[i] = reinterpret_cast<int*>(q);
+    unsigned** uns[4] = {&c->fb.cnt, &c->fb.flag, &c->fb.hoff, &c->fb.hcur};
+    for (int i = 0; i < 4; ++i, q += b4) *uns[i] = reinterpret_cast<unsigned*>(q);
+    unsigned** cells[3] = {&c->fb.counts, &c->fb.off, &c->fb.cur};
+    for (int i = 0; i < 3; ++i, q += bc) *cells[i] = reinterpret_cast<unsigned*>(q);
+    c->fb.seg = reinterpret_cast<unsigned*>(q);
+  }
+  if (capacity > c->fof_sums_cap) {
+    if (c->fof_sums) {
+      COLA_TRY(cuda_status(cudaStreamSynchronize(c->stream), "fof realloc"));
+      cudaFree(c->fof_sums);
+      c->fof_sums = nullptr;
+      c->fof_sums_cap = 0;
+    }
+    void* mem = nullptr;
+    COLA_TRY(cuda_status(cudaMalloc(&mem, (size_t)3 * capacity * sizeof(unsigned long long)), "cudaMalloc fof"));
+    c->fof_sums = mem;
+    c->fof_sums_cap = capacity;
+  }
+  c->fb.sums = static_cast<unsigned long long*>(c->fof_sums);
+  return COLA_OK;
+}
+
+}  // namespace
+
+extern "C" int cola_fof(cola_ctx* c, const float* s, double b, int n_min, int* label, int* size, int* halo_label,
+                        int* halo_size, double* halo_pos, int capacity, int* nhalo) {
+  if (!c || !(b > 0.0) || n_min < 1 || capacity < 0 || c->pg.npart > 0x7fffffffLL) return COLA_ERR_INVALID;
+  for (const void* p : {(const void*)s, (const void*)label, (const void*)size, (const void*)nhalo})
+    COLA_TRY(check_ptr(p));
+  for (const void* p : {(const void*)halo_label, (const void*)halo_size, (const void*)halo_pos})
+    if (p) COLA_TRY(check_ptr(p));
+  FofGeom f;
+  if (!fof_geometry(c->p.nmesh, c->p.np, b, &f)) return COLA_ERR_INVALID;
+  COLA_TRY(fof_workspace(c, f, capacity));
+  return STAGED(kStFof, launch_fof(c->pg, f, s, c->fb, n_min, label, size, halo_label, halo_size, halo_pos, capacity,
+                                   nhalo, c->flags, c->stream));
 }
 
 // ---- reverse mode ---------------------------------------------------------------------------

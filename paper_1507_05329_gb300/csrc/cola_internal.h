@@ -192,6 +192,36 @@ int launch_grid_density_adjoint(const ParticleGeom& pg, const float* s, int ngri
 int launch_snapshot(long long npart, const float* s, const float* v, const float* psi1, const float* psi2, float alpha,
                     float b1, float b2, float g1, float g2, float* s_out, float* v_out, cudaStream_t st);
 
+// Friends-of-friends (fof.cu): geometry of the cell search and work buffers.
+struct FofGeom {
+  long long modulus = 0;   // N 2^20
+  long long ell = 0;       // linking length in fixed-point units
+  long long ncells = 0;    // ncs^3
+  int ncs = 0;             // cells per axis, side >= ell
+};
+struct FofBuffers {
+  long long* g[3] = {nullptr, nullptr, nullptr};   // fixed-point coordinates [n] per axis
+  int* key = nullptr;                              // cell of each particle
+  int* sorted = nullptr;                           // particle ids sorted by cell
+  int* parent = nullptr;                           // union-find forest
+  unsigned* cnt = nullptr;                         // members per root
+  unsigned* flag = nullptr;                        // 1 for roots of haloes
+  unsigned* hoff = nullptr;                        // [n + 1] halo index of each root
+  unsigned* hcur = nullptr;
+  unsigned* counts = nullptr;                      // [ncells] particles per cell
+  unsigned* off = nullptr;                         // [ncells + 1]
+  unsigned* cur = nullptr;
+  unsigned* seg = nullptr;                         // scan segment sums
+  unsigned long long* sums = nullptr;              // [3][capacity] offset sums of the haloes
+};
+bool fof_geometry(int nmesh, int np, double b, FofGeom* f);
+int launch_fof(const ParticleGeom& pg, const FofGeom& f, const float* s, const FofBuffers& fb, int n_min, int* label,
+               int* size, int* halo_label, int* halo_size, double* halo_pos, int capacity, int* nhalo, int* flags,
+               cudaStream_t st);
+// Exclusive scan of m counts into off[0..m] and a copy cur[0..m) (binning.cu); seg holds
+// ceil(m / 4096) partial sums.
+int launch_excl_scan(const unsigned* cnt, int m, unsigned* seg, unsigned* off, unsigned* cur, cudaStream_t st);
+
 // Power spectrum binning of a forward spectrum (side n).
 int launch_pk_bins(const Grid3& g, const float2* dk, const long long* edges, int nbins, double pscale, double kfund,
                    int cic_correct, double shot, double* partials, int nblocks, cudaStream_t st);
@@ -239,4 +269,10 @@ struct cola_ctx {
   void* adj_mem = nullptr;
   float* lam[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // lam_s, lam_v, lam_psi1, lam_psi2, lam_F
   float2* adj_mesh[3] = {nullptr, nullptr, nullptr};
+  // friends-of-friends work space (allocated by cola_fof, grown when a call needs more)
+  void* fof_mem = nullptr;
+  long long fof_ncells = 0;                // cell capacity of fof_mem
+  void* fof_sums = nullptr;
+  int fof_sums_cap = 0;
+  cola::FofBuffers fb;
 };

@@ -120,3 +120,24 @@ def test_matches_breadth_first_search_on_float_distances():
     assert _groups(r["label"]) == _groups(label)
     assert np.array_equal(r["label"], label)        # BFS from increasing starts labels by min id
     assert len(set(label.tolist())) < n // 4        # the configuration is really clustered
+
+
+@pytest.mark.parametrize("b", [0.2, 0.37, 0.6])
+def test_kdtree_candidates_equal_brute_force(b):
+    """The k-d tree search used for large inputs finds exactly the brute-force friend pairs."""
+    rng = np.random.default_rng(int(b * 100))
+    npd, nm = 10, 20
+    q = cic.lattice_indices(npd).astype(np.float64) * (nm / npd)
+    centres = rng.uniform(0, nm, size=(3, 30))
+    x = centres[:, rng.integers(0, 30, size=npd ** 3)] + rng.normal(0, 0.5, size=(3, npd ** 3))
+    s = (x - q).astype(np.float32)
+    g = cic.fixed_point_coords(s, npd, nm)
+    ell = fof.linking_length_fixed(b, npd, nm)
+    i1, j1 = fof.friend_pairs(g, nm, ell)
+    i2, j2 = fof.friend_pairs_kdtree(g, nm, ell)
+    assert i1.size > 100
+    assert sorted(zip(i1.tolist(), j1.tolist())) == sorted(zip(i2.tolist(), j2.tolist()))
+    a = fof.fof(s, npd, nm, b, n_min=3, search="brute")
+    k = fof.fof(s, npd, nm, b, n_min=3, search="kdtree")
+    for key in ("label", "size", "halo_label", "halo_size", "halo_pos"):
+        assert np.array_equal(a[key], k[key]), key
