@@ -302,13 +302,14 @@ int cola_fof(cola_ctx* ctx, const float* s, double b, int n_min, int* label, int
  * the fused stage 3 (P(k), density spectrum, 2LPT), 8 2LPT element-wise kernels, 9 P(k) binning,
  * 10 mesh clearing (memset, direct deposit only), 11 spatial binning of the particles (count, scan,
  * scatter), 12 reverse-mode and loss-grid kernels (adjoint element-wise maps, adjoint scatter and
- * gather, loss-grid deposit), 13 friends-of-friends.  Stages 1, 2, 4, 5 and 7 also count the 2LPT and adjoint transforms.
+ * gather, loss-grid deposit), 13 friends-of-friends, 14 the 2LPT lattice transforms (forward and
+ * adjoint).  Stages 1, 2, 4, 5 and 7 also count the adjoint's mesh transforms.
  * cola_profile_enable(ctx, 1) resets the totals and brackets every later launch with CUDA events
  * on the context's stream; 0 stops timing (launches are always counted).  cola_profile_read
  * synchronises the stream and writes per-stage total milliseconds and launch counts for the first
- * nstages stages (either pointer may be NULL).  Returns the number of stages (14), or minus a
+ * nstages stages (either pointer may be NULL).  Returns the number of stages (15), or minus a
  * cola_status on failure. */
-#define COLA_NUM_STAGES 14
+#define COLA_NUM_STAGES 15
 int cola_profile_enable(cola_ctx* ctx, int on);
 int cola_profile_read(cola_ctx* ctx, double* ms, long long* launches, int nstages);
 

@@ -106,7 +106,7 @@ class BatchIO(ctypes.Structure):
     _fields_ = [("white_noise", _VP), ("s", _VP), ("v", _VP), ("psi1", _VP), ("psi2", _VP), ("pk", _VP)]
 
 STAGES = ["deposit", "fwd_z_r2c", "fwd_y", "green_x", "inv_y", "inv_z_c2r", "gather_kick_drift", "x_pass",
-          "ic_elementwise", "pk_bins", "clear", "bin", "adjoint", "fof"]
+          "ic_elementwise", "pk_bins", "clear", "bin", "adjoint", "fof", "ic_fft"]
 
 
 def load_library(path: str = LIB_PATH):

@@ -260,6 +260,7 @@ struct cola_ctx {
   void* bin_mem = nullptr;
   // measurement support
   bool prof = false;
+  bool lattice_fft = false;   // the 2LPT lattice transforms are running (their own stage)
   double stage_ms[COLA_NUM_STAGES] = {};
   long long stage_launches[COLA_NUM_STAGES] = {};
   struct Mark { int stage; cudaEvent_t a, b; };

@@ -541,6 +541,85 @@ struct RealPairDst {   // (re, im) -> real rows (2w, 2w+1)
 
 __device__ __forceinline__ int fast_tile_elems(int n, int lw) { return (n + n / 16 + 1) << lw; }
 
+// Writes i dy v to base1 and i dz[w] v to base2 (W adjacent columns of two strided pencils).
+struct PencilG2 {
+  float2* base1;
+  float2* base2;
+  long long jstride;
+  int cols_left;   // nc - col0
+  float dy;
+  const float* dz;   // gradient kernel at the tile's columns
+  __device__ __forceinline__ void operator()(int j, int w, float2 v) const {
+    if (w < cols_left) {
+      const float d = dz[w];
+      base1[j * jstride + w] = make_float2(-dy * v.y, dy * v.x);
+      base2[j * jstride + w] = make_float2(-d * v.y, d * v.x);
+    }
+  }
+  __device__ __forceinline__ void st2(int j, int w, float4 v) const {
+    if (w + 1 < cols_left) {
+      const float d0 = dz[w], d1 = dz[w + 1];
+      *reinterpret_cast<float4*>(base1 + j * jstride + w) = make_float4(-dy * v.y, dy * v.x, -dy * v.w, dy * v.z);
+      *reinterpret_cast<float4*>(base2 + j * jstride + w) = make_float4(-d0 * v.y, d0 * v.x, -d1 * v.w, d1 * v.z);
+    } else {
+      (*this)(j, w, make_float2(v.x, v.y));
+    }
+  }
+};
+
+// Inverse x transform of the register-resident spectrum (times i D_x(k_x) when GRADX) into gout:
+// the transposed last stage straight from registers, then the remaining stages in shared memory.
+template <int RL, int MAXR, bool GRADX, class GDst>
+__device__ __forceinline__ void green_inverse(const FastPlan& p, int lw, const float2 (&spec)[(kEpt + RL - 1) / RL][RL],
+                                              const float* __restrict__ dtab, const GDst& gout, float2* a, float2* b) {
+  constexpr int kB = (kEpt + RL - 1) / RL;
+  const int n = p.n, tid = threadIdx.x, nt = blockDim.x, m = p.nst;
+  const int nb = n / RL, total = nb << lw, wm = (1 << lw) - 1;
+  const int ls = p.lns[m - 1], tstr = p.tstr[m - 1];
+  float2* cur = a;
+  float2* nxt = b;
+#pragma unroll
+  for (int i = 0; i < kB; ++i) {
+    const int idx = tid + i * nt;
+    if (idx < total) {
+      const int w = idx & wm, bb = idx >> lw;
+      float2 v[RL];
+#pragma unroll
+      for (int r = 0; r < RL; ++r) {
+        if (GRADX) {
+          const float d = dtab[bb + (r << ls)];
+          v[r] = make_float2(-d * spec[i][r].y, d * spec[i][r].x);   // i D g delta
+        } else {
+          v[r] = spec[i][r];
+        }
+      }
+      // transposed last stage (first of the inverse): inputs are exactly v
+      Dft<RL, +1>::run(v);
+      if (ls) {
+#pragma unroll
+        for (int r = 1; r < RL; ++r) v[r] = cmul(v[r], twid<+1>(p.tw, r * bb * tstr));
+      }
+#pragma unroll
+      for (int r = 0; r < RL; ++r) {
+        if (m > 1) cur[saddr(bb + r * nb, w, lw)] = v[r];
+        else gout(bb + r * nb, w, v[r]);
+      }
+    }
+  }
+  if (m > 1) {
+    __syncthreads();
+    for (int s = m - 2; s > 0; --s) {
+      any_stage<true, +1, MAXR>(p, s, lw, SmemR{cur, lw}, SmemW{nxt, lw}, tid, nt);
+      __syncthreads();
+      float2* t = cur;
+      cur = nxt;
+      nxt = t;
+    }
+    any_stage<true, +1, MAXR>(p, 0, lw, SmemR{cur, lw}, gout, tid, nt);
+    __syncthreads();   // before the next inverse reuses the buffers
+  }
+}
+
 // x pass fused with Green function and gradient kernel, spectrum kept in registers between the
 // forward transform's last stage and the inverse transforms' first (transposed) stage.
 template <int RL, int MAXR>
@@ -597,54 +676,13 @@ __device__ __forceinline__ void green_body(const FastPlan& p, int lw, const floa
     }
   }
   __syncthreads();   // the forward's shared buffers are free from here on
-  const float dy = dtab[y];
-  a = sm;
-  b = sm + fast_tile_elems(n, lw);
-#pragma unroll 1
-  for (int comp = 0; comp < 3; ++comp) {
-    float2* o = comp == 0 ? out0 : (comp == 1 ? out1 : out2);
-    const PencilG gout{o + boff, jstride, nc - col0};
-    float2* cur = a;
-    float2* nxt = b;
-#pragma unroll
-    for (int i = 0; i < kB; ++i) {
-      const int idx = tid + i * nt;
-      if (idx < total) {
-        const int w = idx & wm, bb = idx >> lw;
-        const int mz = col0 + w;
-        float2 v[RL];
-#pragma unroll
-        for (int r = 0; r < RL; ++r) {
-          const int j = bb + (r << ls);
-          const float d = comp == 0 ? dtab[j] : (comp == 1 ? dy : (mz < nc ? dtab[mz] : 0.0f));
-          v[r] = make_float2(-d * spec[i][r].y, d * spec[i][r].x);   // i D g delta
-        }
-        // transposed last stage (first of the inverse): inputs are exactly v
-        Dft<RL, +1>::run(v);
-        if (ls) {
-#pragma unroll
-          for (int r = 1; r < RL; ++r) v[r] = cmul(v[r], twid<+1>(p.tw, r * bb * tstr));
-        }
-#pragma unroll
-        for (int r = 0; r < RL; ++r) {
-          if (m > 1) cur[saddr(bb + r * nb, w, lw)] = v[r];
-          else gout(bb + r * nb, w, v[r]);
-        }
-      }
-    }
-    if (m > 1) {
-      __syncthreads();
-      for (int s = m - 2; s > 0; --s) {
-        any_stage<true, +1, MAXR>(p, s, lw, SmemR{cur, lw}, SmemW{nxt, lw}, tid, nt);
-        __syncthreads();
-        float2* t = cur;
-        cur = nxt;
-        nxt = t;
-      }
-      any_stage<true, +1, MAXR>(p, 0, lw, SmemR{cur, lw}, gout, tid, nt);
-      __syncthreads();   // before the next component reuses the buffers
-    }
-  }
+  // D_y(k_y) and D_z(k_z) are constant along an x pencil, so F_y and F_z are i D_y H and i D_z H of
+  // one inverse H = IFFT_x(g delta): two inverse transforms instead of three
+  green_inverse<RL, MAXR, true>(p, lw, spec, dtab, PencilG{out0 + boff, jstride, nc - col0}, sm,
+                                sm + fast_tile_elems(n, lw));
+  green_inverse<RL, MAXR, false>(p, lw, spec, dtab,
+                                 PencilG2{out1 + boff, out2 + boff, jstride, nc - col0, dtab[y], dtab + col0}, sm,
+                                 sm + fast_tile_elems(n, lw));
 }
 
 // =============================================================================================
