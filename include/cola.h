@@ -143,6 +143,12 @@ int cola_power_spectrum(cola_ctx* ctx, const float* s, double* pk, int nbins);
  *                               and tiles of at least 4 cells along z).
  *   COLA_SCHED_PIPELINED_FFT  : persistent cp.async-pipelined strided FFT passes (else one CTA per
  *                               tile of pencils).
+ *   COLA_SCHED_PIPE_EPT8      : the pipelined passes give each thread 8 complex values per stage
+ *                               instead of 16 (twice the threads on the same tile); requires
+ *                               COLA_SCHED_PIPELINED_FFT.
+ *   COLA_SCHED_PIPELINED_GATHER: the tile gather runs on persistent CTAs that copy the next tile's
+ *                               forces while interpolating the current one (requires
+ *                               COLA_SCHED_TILE_GATHER).
  *   bits COLA_SCHED_BUDGET_SHIFT..+1 : shared-memory budget per CTA of the pipelined passes,
  *                               0: 160 KB, 1: 96 KB, 2: 64 KB (sets their tile width); must be 0
  *                               without COLA_SCHED_PIPELINED_FFT.
@@ -157,6 +163,8 @@ int cola_power_spectrum(cola_ctx* ctx, const float* s, double* pk, int nbins);
 #define COLA_SCHED_BINNED_DEPOSIT 1
 #define COLA_SCHED_TILE_GATHER 2
 #define COLA_SCHED_PIPELINED_FFT 4
+#define COLA_SCHED_PIPE_EPT8 8
+#define COLA_SCHED_PIPELINED_GATHER 16
 #define COLA_SCHED_BUDGET_SHIFT 8
 int cola_get_schedule(cola_ctx* ctx, int* schedule);
 int cola_set_schedule(cola_ctx* ctx, int schedule);

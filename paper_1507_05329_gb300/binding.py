@@ -99,6 +99,8 @@ PK_CIC_CORRECT = 1
 SCHED_BINNED_DEPOSIT = 1
 SCHED_TILE_GATHER = 2
 SCHED_PIPELINED_FFT = 4
+SCHED_PIPE_EPT8 = 8
+SCHED_PIPELINED_GATHER = 16
 SCHED_BUDGET_SHIFT = 8
 
 

@@ -306,56 +306,59 @@ __global__ void __launch_bounds__(kThreads) k_deposit_tiles(ParticleGeom pg, Bin
 
 // Tile-wise gather (+ kick and drift) over the primary entries of each tile, from a shared copy
 // of the tile's force values with a one-cell halo on the upper side of every axis.
-template <bool KICK>
-__global__ void __launch_bounds__(kThreads) k_gather_tiles(ParticleGeom pg, BinGeom b, int gz,
-                                                          const unsigned* __restrict__ off_p,
-                                                          const unsigned* __restrict__ ent_p,
-                                                          const float* __restrict__ f0, const float* __restrict__ f1,
-                                                          const float* __restrict__ f2, long long rs,
-                                                          const float* __restrict__ s_in, float* __restrict__ force_out,
-                                                          float* s, float* v, const float* __restrict__ psi1,
-                                                          const float* __restrict__ psi2, KickDrift kd, int* flags) {
-  // one CTA: gz consecutive tiles along z (their entries are contiguous), i.e. T x T x (gz TZ) cells.
-  // Shared copy: 3 components x (T+1)^2 rows of hz = gz TZ + 1 floats, rows padded to hp (16 B).
-  extern __shared__ __align__(16) float fsm[];
-  const int nm = pg.n, T = 1 << b.lt;
-  const int tile = blockIdx.x * gz;
+// Shared copy: 3 components x (T+1)^2 rows of hz = TZ + 1 floats, rows padded to hp (16 B).
+struct GatherTile {
+  int x0, y0, z0;
+};
+
+__device__ __forceinline__ GatherTile gather_tile_origin(const BinGeom& b, int tile) {
   const int bz = tile % b.nz, bxy = tile / b.nz;
   const int bx = bxy / b.nt, by = bxy - bx * b.nt;
-  const int x0 = bx << b.lt, y0 = by << b.lt, z0 = bz << b.lz;
-  const int hx = T + 1, zl = gz << b.lz, hz = zl + 1, hp = (hz + 3) & ~3;
-  const int rows = 3 * hx * hx;
-  const unsigned e0 = off_p[tile], e1 = off_p[tile + gz];
-  if (e0 == e1) return;                          // empty (uniform across the block)
-  {
-    // asynchronous copies: zl/4 chunks of 16 bytes (rows start 16-byte aligned: z0 is a multiple of
-    // TZ and real rows hold 2 pc floats, pc even) plus the 4-byte halo cell, all in flight at once
-    const int chunks = (zl >> 2) + 1;
-    for (int op = threadIdx.x; op < rows * chunks; op += blockDim.x) {
-      const int r = op / chunks, ch = op - r * chunks;
-      const int comp = r / (hx * hx), col = r - comp * hx * hx;
-      const int lx = col / hx, ly = col - lx * hx;
-      int gx = x0 + lx, gy = y0 + ly;
-      if (gx >= nm) gx -= nm;
-      if (gy >= nm) gy -= nm;
-      const float* f = comp == 0 ? f0 : (comp == 1 ? f1 : f2);
-      const float* row = f + ((long long)gx * nm + gy) * rs;
-      float* dst = fsm + r * hp;
-      if (ch < (zl >> 2)) {
-        const unsigned sa = (unsigned)__cvta_generic_to_shared(dst + 4 * ch);
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(row + z0 + 4 * ch) : "memory");
-      } else {
-        const int gzz = z0 + zl == nm ? 0 : z0 + zl;   // periodic halo cell
-        const unsigned sa = (unsigned)__cvta_generic_to_shared(dst + zl);
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(row + gzz) : "memory");
-      }
+  return GatherTile{bx << b.lt, by << b.lt, bz << b.lz};
+}
+
+// Issue (and commit as one group) the asynchronous copies of a tile's forces into fsm: TZ/4
+// chunks of 16 bytes per row (rows start 16-byte aligned: z0 is a multiple of TZ and real rows
+// hold 2 pc floats, pc even) plus the 4-byte periodic halo cell.
+__device__ __forceinline__ void gather_stage(float* fsm, const BinGeom& b, int nm, const GatherTile& t,
+                                             const float* __restrict__ f0, const float* __restrict__ f1,
+                                             const float* __restrict__ f2, long long rs) {
+  const int hx = (1 << b.lt) + 1, zl = 1 << b.lz, hp = (zl + 1 + 3) & ~3;
+  const int rows = 3 * hx * hx, chunks = (zl >> 2) + 1;
+  for (int op = threadIdx.x; op < rows * chunks; op += blockDim.x) {
+    const int r = op / chunks, ch = op - r * chunks;
+    const int comp = r / (hx * hx), col = r - comp * hx * hx;
+    const int lx = col / hx, ly = col - lx * hx;
+    int gx = t.x0 + lx, gy = t.y0 + ly;
+    if (gx >= nm) gx -= nm;
+    if (gy >= nm) gy -= nm;
+    const float* f = comp == 0 ? f0 : (comp == 1 ? f1 : f2);
+    const float* row = f + ((long long)gx * nm + gy) * rs;
+    float* dst = fsm + r * hp;
+    if (ch < (zl >> 2)) {
+      const unsigned sa = (unsigned)__cvta_generic_to_shared(dst + 4 * ch);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(row + t.z0 + 4 * ch) : "memory");
+    } else {
+      const int gzz = t.z0 + zl == nm ? 0 : t.z0 + zl;
+      const unsigned sa = (unsigned)__cvta_generic_to_shared(dst + zl);
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(row + gzz) : "memory");
     }
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
-    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
   }
-  __syncthreads();
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+// Interpolate the staged forces at the tile's particles e0..e1 (and kick and drift).  Returns
+// whether a non-finite state was written.
+template <bool KICK>
+__device__ __forceinline__ bool gather_particles(const float* fsm, const ParticleGeom& pg, const BinGeom& b,
+                                                 const GatherTile& t, unsigned e0, unsigned e1,
+                                                 const unsigned* __restrict__ ent_p, const float* __restrict__ s_in,
+                                                 float* __restrict__ force_out, float* s, float* v,
+                                                 const float* __restrict__ psi1, const float* __restrict__ psi2,
+                                                 const KickDrift& kd) {
+  const int hx = (1 << b.lt) + 1, hp = ((1 << b.lz) + 1 + 3) & ~3;
   const long long n = pg.npart;
-  const long long modulus = (long long)nm << kFracBits;
+  const long long modulus = (long long)pg.n << kFracBits;
   const float inv_one = 1.0f / kWeightOne;
   bool bad = false;
 #pragma unroll 2
@@ -364,7 +367,16 @@ __global__ void __launch_bounds__(kThreads) k_gather_tiles(ParticleGeom pg, BinG
     long long id;
     unpack_q(ent_p[e], pg.np, q, &id);
     const float* sp = KICK ? s : s_in;
-    float sv[3];
+    float sv[3], pv1[3], pv2[3], vv[3];
+    if (KICK) {
+      // issue every particle load up front: their latency overlaps the interpolation below
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        pv1[a] = __ldg(psi1 + a * n + id);
+        pv2[a] = __ldg(psi2 + a * n + id);
+        vv[a] = v[a * n + id];
+      }
+    }
     int c[3];
     float w1[3];
 #pragma unroll
@@ -374,7 +386,7 @@ __global__ void __launch_bounds__(kThreads) k_gather_tiles(ParticleGeom pg, BinG
       c[a] = (int)(g >> kFracBits);
       w1[a] = (float)((int)(g >> (kFracBits - 14)) & (kWeightOne - 1)) * inv_one;
     }
-    const int lx = c[0] - x0, ly = c[1] - y0, lz = c[2] - z0;   // base cell inside the tile
+    const int lx = c[0] - t.x0, ly = c[1] - t.y0, lz = c[2] - t.z0;   // base cell inside the tile
     float fr[3] = {0.f, 0.f, 0.f};
 #pragma unroll
     for (int dx = 0; dx < 2; ++dx) {
@@ -397,9 +409,9 @@ __global__ void __launch_bounds__(kThreads) k_gather_tiles(ParticleGeom pg, BinG
     } else {
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        const float p1 = __ldg(psi1 + a * n + id), p2 = __ldg(psi2 + a * n + id);
+        const float p1 = pv1[a], p2 = pv2[a];
         const float fres = fr[a] - (kd.c1 * p1 + kd.c2 * p2);
-        const float vn = v[a * n + id] + kd.kick * fres;
+        const float vn = vv[a] + kd.kick * fres;
         const float sn = sv[a] + kd.drift * vn + kd.dd1 * p1 + kd.dd2 * p2;
         v[a * n + id] = vn;
         s[a * n + id] = sn;
@@ -407,6 +419,72 @@ __global__ void __launch_bounds__(kThreads) k_gather_tiles(ParticleGeom pg, BinG
       }
     }
   }
+  return bad;
+}
+
+// One CTA per tile.
+template <bool KICK>
+__global__ void __launch_bounds__(kThreads) k_gather_tiles(ParticleGeom pg, BinGeom b,
+                                                          const unsigned* __restrict__ off_p,
+                                                          const unsigned* __restrict__ ent_p,
+                                                          const float* __restrict__ f0, const float* __restrict__ f1,
+                                                          const float* __restrict__ f2, long long rs,
+                                                          const float* __restrict__ s_in, float* __restrict__ force_out,
+                                                          float* s, float* v, const float* __restrict__ psi1,
+                                                          const float* __restrict__ psi2, KickDrift kd, int* flags) {
+  extern __shared__ __align__(16) float fsm[];
+  const int tile = blockIdx.x;
+  const unsigned e0 = off_p[tile], e1 = off_p[tile + 1];
+  if (e0 == e1) return;                          // empty (uniform across the block)
+  const GatherTile t = gather_tile_origin(b, tile);
+  gather_stage(fsm, b, pg.n, t, f0, f1, f2, rs);
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+  __syncthreads();
+  const bool bad = gather_particles<KICK>(fsm, pg, b, t, e0, e1, ent_p, s_in, force_out, s, v, psi1, psi2, kd);
+  if (KICK && __syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flags, 2);
+}
+
+// Persistent variant: each CTA walks tiles t = blockIdx.x + i gridDim.x with two staging buffers;
+// the next non-empty tile's forces are copied (cp.async) while the current tile's particles run.
+template <bool KICK>
+__global__ void __launch_bounds__(kThreads) k_gather_tiles_pipe(ParticleGeom pg, BinGeom b,
+                                                               const unsigned* __restrict__ off_p,
+                                                               const unsigned* __restrict__ ent_p,
+                                                               const float* __restrict__ f0,
+                                                               const float* __restrict__ f1,
+                                                               const float* __restrict__ f2, long long rs,
+                                                               const float* __restrict__ s_in,
+                                                               float* __restrict__ force_out, float* s, float* v,
+                                                               const float* __restrict__ psi1,
+                                                               const float* __restrict__ psi2, KickDrift kd,
+                                                               int* flags) {
+  extern __shared__ __align__(16) float fsm[];
+  const int hx = (1 << b.lt) + 1, hp = ((1 << b.lz) + 1 + 3) & ~3;
+  float* bcur = fsm;
+  float* bnext = fsm + 3 * hx * hx * hp;
+  const int ntiles = b.tiles;
+  // first non-empty tile of this CTA
+  auto next_tile = [&](int t) {
+    while (t < ntiles && off_p[t] == off_p[t + 1]) t += gridDim.x;
+    return t;
+  };
+  int t = next_tile(blockIdx.x);
+  if (t >= ntiles) return;
+  gather_stage(bcur, b, pg.n, gather_tile_origin(b, t), f0, f1, f2, rs);
+  bool bad = false;
+  while (t < ntiles) {
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    __syncthreads();   // tile t staged; every thread is done with the other buffer
+    const int tn = next_tile(t + gridDim.x);
+    if (tn < ntiles) gather_stage(bnext, b, pg.n, gather_tile_origin(b, tn), f0, f1, f2, rs);
+    bad |= gather_particles<KICK>(bcur, pg, b, gather_tile_origin(b, t), off_p[t], off_p[t + 1], ent_p, s_in,
+                                  force_out, s, v, psi1, psi2, kd);
+    float* tmp = bcur;
+    bcur = bnext;
+    bnext = tmp;
+    t = tn;
+  }
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
   if (KICK && __syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flags, 2);
 }
 
@@ -467,14 +545,16 @@ int launch_binning(const ParticleGeom& pg, const BinGeom& b, const float* s, Bin
     cudaFuncSetAttribute(k_deposit_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
     cudaFuncSetAttribute(k_gather_tiles<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
     cudaFuncSetAttribute(k_gather_tiles<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+    cudaFuncSetAttribute(k_gather_tiles_pipe<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024);
+    cudaFuncSetAttribute(k_gather_tiles_pipe<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024);
     attr = true;
   }
-  if (cudaMemsetAsync(bb.cnt_p, 0, (size_t)b.tiles * sizeof(unsigned), st) != cudaSuccess ||
-      cudaMemsetAsync(bb.cnt_s, 0, (size_t)b.tiles * sizeof(unsigned), st) != cudaSuccess)
-    return COLA_ERR_CUDA;
   const long long rows = (long long)pg.np * pg.np;
   const unsigned grid = (unsigned)(rows < 152LL * 64 ? rows : 152LL * 64);
   const int th = pg.np < kThreads ? ((pg.np + 31) / 32) * 32 : kThreads;
+  if (cudaMemsetAsync(bb.cnt_p, 0, (size_t)b.tiles * sizeof(unsigned), st) != cudaSuccess ||
+      cudaMemsetAsync(bb.cnt_s, 0, (size_t)b.tiles * sizeof(unsigned), st) != cudaSuccess)
+    return COLA_ERR_CUDA;
   k_bin<false><<<grid, th, 0, st>>>(pg, b, s, bb.cnt_p, bb.cnt_s, nullptr, nullptr);
   int e = check_launch("bin_count");
   if (e != COLA_OK) return e;
@@ -497,17 +577,32 @@ int launch_deposit_tiles(const ParticleGeom& pg, const BinGeom& b, const float* 
 
 int launch_gather_tiles(const ParticleGeom& pg, const BinGeom& b, const BinBuffers& bb, const float* const f[3],
                         long long rs, const float* s_in, float* force_out, float* s, float* v, const float* psi1,
-                        const float* psi2, const KickDrift* kd, int* flags, cudaStream_t st) {
+                        const float* psi2, const KickDrift* kd, int* flags, cudaStream_t st, bool pipelined) {
   const size_t sm = gather_smem_bytes(b);
-  const int gz = gather_group(b);
-  const int blocks = b.tiles / gz;
+  const KickDrift k = kd ? *kd : KickDrift{};
+  if (pipelined) {
+    // two staging buffers per CTA: as many CTAs per SM as the shared memory holds (at most 4)
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int per_sm = (int)((227 * 1024) / (2 * sm + 1024));
+    if (per_sm > 4) per_sm = 4;
+    if (per_sm < 1) per_sm = 1;
+    const int ctas = b.tiles < sms * per_sm ? b.tiles : sms * per_sm;
+    if (kd)
+      k_gather_tiles_pipe<true><<<ctas, kThreads, 2 * sm, st>>>(pg, b, bb.off_p, bb.ent_p, f[0], f[1], f[2], rs,
+                                                                 nullptr, nullptr, s, v, psi1, psi2, k, flags);
+    else
+      k_gather_tiles_pipe<false><<<ctas, kThreads, 2 * sm, st>>>(pg, b, bb.off_p, bb.ent_p, f[0], f[1], f[2], rs, s_in,
+                                                                  force_out, nullptr, nullptr, nullptr, nullptr, k,
+                                                                  flags);
+    return check_launch("gather_tiles_pipe");
+  }
   if (kd)
-    k_gather_tiles<true><<<blocks, kThreads, sm, st>>>(pg, b, gz, bb.off_p, bb.ent_p, f[0], f[1], f[2], rs, nullptr,
-                                                        nullptr, s, v, psi1, psi2, *kd, flags);
+    k_gather_tiles<true><<<b.tiles, kThreads, sm, st>>>(pg, b, bb.off_p, bb.ent_p, f[0], f[1], f[2], rs, nullptr,
+                                                         nullptr, s, v, psi1, psi2, k, flags);
   else
-    k_gather_tiles<false><<<blocks, kThreads, sm, st>>>(pg, b, gz, bb.off_p, bb.ent_p, f[0], f[1], f[2], rs, s_in,
-                                                         force_out, nullptr, nullptr, nullptr, nullptr, KickDrift{},
-                                                         flags);
+    k_gather_tiles<false><<<b.tiles, kThreads, sm, st>>>(pg, b, bb.off_p, bb.ent_p, f[0], f[1], f[2], rs, s_in,
+                                                          force_out, nullptr, nullptr, nullptr, nullptr, k, flags);
   return check_launch("gather_tiles");
 }
 

@@ -137,7 +137,7 @@ int gather(cola_ctx* c, const float* s_in, float* force, float* s, float* v, con
                        reinterpret_cast<float*>(c->cbuf[2])};
   if (c->binned && c->tile_gather)
     return STAGED(kStGather, launch_gather_tiles(c->pg, c->bg, c->bb, f, 2LL * c->mesh.pc, s_in, force, s, v, psi1,
-                                                 psi2, kd, c->flags, c->stream));
+                                                 psi2, kd, c->flags, c->stream, c->gather_pipe));
   return STAGED(kStGather, launch_gather(c->pg, f, 2LL * c->mesh.pc, s_in, force, s, v, psi1, psi2, kd, c->flags,
                                          c->stream));
 }
@@ -533,13 +533,16 @@ int schedule_of(const cola_ctx* c) {
   int k = 0;
   while (k < 2 && kPipeBudgetsKb[k] != c->mplan.pipe_kb) ++k;
   return (c->binned ? COLA_SCHED_BINNED_DEPOSIT : 0) | (c->tile_gather ? COLA_SCHED_TILE_GATHER : 0) |
-         (c->mplan.pipe ? COLA_SCHED_PIPELINED_FFT : 0) | (k << COLA_SCHED_BUDGET_SHIFT);
+         (c->mplan.pipe ? COLA_SCHED_PIPELINED_FFT : 0) | (c->mplan.pipe_ept == 8 ? COLA_SCHED_PIPE_EPT8 : 0) |
+         (c->gather_pipe ? COLA_SCHED_PIPELINED_GATHER : 0) | (k << COLA_SCHED_BUDGET_SHIFT);
 }
 
 bool schedule_valid(const cola_ctx* c, int sc) {
-  if (sc & ~(COLA_SCHED_BINNED_DEPOSIT | COLA_SCHED_TILE_GATHER | COLA_SCHED_PIPELINED_FFT |
-             (3 << COLA_SCHED_BUDGET_SHIFT)))
+  if (sc & ~(COLA_SCHED_BINNED_DEPOSIT | COLA_SCHED_TILE_GATHER | COLA_SCHED_PIPELINED_FFT | COLA_SCHED_PIPE_EPT8 |
+             COLA_SCHED_PIPELINED_GATHER | (3 << COLA_SCHED_BUDGET_SHIFT)))
     return false;
+  if ((sc & COLA_SCHED_PIPELINED_GATHER) && !(sc & COLA_SCHED_TILE_GATHER)) return false;
+  if ((sc & COLA_SCHED_PIPE_EPT8) && !(sc & COLA_SCHED_PIPELINED_FFT)) return false;   // unused knob
   if ((sc & COLA_SCHED_BINNED_DEPOSIT) && !c->bin_mem) return false;
   if ((sc & COLA_SCHED_TILE_GATHER) && !(sc & COLA_SCHED_BINNED_DEPOSIT)) return false;
   if ((sc & COLA_SCHED_TILE_GATHER) && c->bg.lz < 2) return false;   // 16-byte staging copies along z
@@ -553,6 +556,8 @@ void apply_schedule(cola_ctx* c, int sc) {
   c->tile_gather = (sc & COLA_SCHED_TILE_GATHER) != 0;
   c->mplan.pipe = (sc & COLA_SCHED_PIPELINED_FFT) != 0;
   c->mplan.pipe_kb = kPipeBudgetsKb[(sc >> COLA_SCHED_BUDGET_SHIFT) & 3];
+  c->mplan.pipe_ept = (sc & COLA_SCHED_PIPE_EPT8) ? 8 : 16;
+  c->gather_pipe = (sc & COLA_SCHED_PIPELINED_GATHER) != 0;
 }
 }  // namespace
 

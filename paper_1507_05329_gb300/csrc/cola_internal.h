@@ -56,6 +56,7 @@ struct FftPlan {
   // on/off, and their shared-memory budget per CTA (sets the tile width)
   bool pipe = true;
   int pipe_kb = 160;
+  int pipe_ept = 16;      // complex elements per thread of the pipelined passes (16 or 8)
 };
 
 // Factor n into radices {16, 8, 5, 4, 3, 2}; returns false if n has another prime factor.
@@ -157,7 +158,8 @@ int launch_deposit_tiles(const ParticleGeom& pg, const BinGeom& b, const float* 
                          unsigned long long* rho, cudaStream_t st);
 int launch_gather_tiles(const ParticleGeom& pg, const BinGeom& b, const BinBuffers& bb, const float* const f[3],
                         long long rs, const float* s_in, float* force_out, float* s, float* v, const float* psi1,
-                        const float* psi2, const KickDrift* kd, int* flags, cudaStream_t st);
+                        const float* psi2, const KickDrift* kd, int* flags, cudaStream_t st,
+                        bool pipelined = false);
 
 // 2LPT helpers on the lattice grid (side np).
 enum IcField { kIcPsi1 = 0, kIcHess = 1, kIcPsi2 = 2 };
@@ -255,6 +257,7 @@ struct cola_ctx {
   unsigned long long* mass_acc = nullptr; // 128-bit total of the fixed-point mesh (overflow check)
   bool binned = false;                    // tile-wise deposit (else direct atomics)
   bool tile_gather = false;               // tile-wise gather from shared memory (else lattice order)
+  bool gather_pipe = false;               // ... by persistent CTAs that stage the next tile meanwhile
   cola::BinGeom bg{};
   cola::BinBuffers bb;
   void* bin_mem = nullptr;

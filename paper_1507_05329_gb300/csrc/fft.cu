@@ -39,22 +39,24 @@ struct PipeShape {
   size_t smem;
 };
 
-PipeShape pipe_shape(const Grid3& g, int budget_kb) {
+PipeShape pipe_shape(const Grid3& g, int budget_kb, int ept) {
   PipeShape ps;
   int lw = 1;   // W >= 2: 16-byte copies
   while ((2 << lw) <= largest_pow2_le(g.nc) &&
-         (size_t)3 * (g.n + g.n / 16 + 1) * (2 << lw) * 8 <= (size_t)budget_kb * 1024)
+         (size_t)3 * (g.n + g.n / 16 + 1) * (2 << lw) * 8 <= (size_t)budget_kb * 1024 &&
+         ((long long)g.n * (2 << lw) + ept - 1) / ept <= kPipeThreads)
     ++lw;
   ps.lw = lw;
   ps.smem = (size_t)3 * (g.n + g.n / 16 + 1) * (1 << lw) * sizeof(float2);
-  int th = ((g.n << lw) + kPipeEpt - 1) / kPipeEpt;
+  int th = ((g.n << lw) + ept - 1) / ept;
   th = ((th + 31) / 32) * 32;
   ps.threads = th < 64 ? 64 : (th > kPipeThreads ? kPipeThreads : th);
   ps.nchunks = (g.nc + (1 << lw) - 1) >> lw;
   ps.ntiles = ps.nchunks * g.n;
   int dev = 0, sms = 152;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int per_sm = ps.smem <= 72 * 1024 ? 3 : (ps.smem <= 110 * 1024 ? 2 : 1);
+  int per_sm = ps.smem <= 72 * 1024 ? 3 : (ps.smem <= 110 * 1024 ? 2 : 1);
+  if (per_sm * ps.threads > 2048) per_sm = 2048 / ps.threads > 0 ? 2048 / ps.threads : 1;
   ps.ctas = ps.ntiles < sms * per_sm ? ps.ntiles : sms * per_sm;
   return ps;
 }
@@ -62,8 +64,8 @@ PipeShape pipe_shape(const Grid3& g, int budget_kb) {
 // The pipelined kernels need at least two columns per tile and a whole tile per thread set.
 bool pipe_ok(const FftPlan& p, const Grid3& g) {
   if (!p.pipe || g.nc < 2) return false;
-  const PipeShape ps = pipe_shape(g, p.pipe_kb);
-  return (long long)ps.threads * kPipeEpt >= (long long)(g.n << ps.lw) && ps.smem <= 200 * 1024;
+  const PipeShape ps = pipe_shape(g, p.pipe_kb, p.pipe_ept);
+  return (long long)ps.threads * p.pipe_ept >= (long long)(g.n << ps.lw) && ps.smem <= 200 * 1024;
 }
 
 int max_radix(const FastPlan& fp) {
@@ -208,13 +210,13 @@ int launch_pencils(const FftPlan& p, const Grid3& g, int axis, int dir, float2* 
   const long long ostride = axis == 1 ? plane : g.pc;
   FastPlan fp;
   if (fast_plan(p, &fp) && pipe_ok(p, g)) {
-    const PipeShape ps = pipe_shape(g, p.pipe_kb);
+    const PipeShape ps = pipe_shape(g, p.pipe_kb, p.pipe_ept);
     if (max_radix(fp) > 8)
-      pipe_pencils_launch<16>(fp, ps.lw, ps.ctas, ps.threads, ps.smem, dir, data, jstride, ostride, g.nc, ps.nchunks,
-                              ps.ntiles, st);
+      pipe_pencils_launch<16>(fp, ps.lw, ps.ctas, ps.threads, ps.smem, dir, p.pipe_ept, data, jstride, ostride, g.nc,
+                              ps.nchunks, ps.ntiles, st);
     else
-      pipe_pencils_launch<8>(fp, ps.lw, ps.ctas, ps.threads, ps.smem, dir, data, jstride, ostride, g.nc, ps.nchunks,
-                             ps.ntiles, st);
+      pipe_pencils_launch<8>(fp, ps.lw, ps.ctas, ps.threads, ps.smem, dir, p.pipe_ept, data, jstride, ostride, g.nc,
+                             ps.nchunks, ps.ntiles, st);
     return check_launch("pencils_pipe");
   }
   if (fast_plan(p, &fp)) {

@@ -296,7 +296,7 @@ __device__ __forceinline__ void tr_stage_pairs(const FastPlan& p, int s, int lw,
 template <int R, int DIR, class Src, class Dst, int EPT = kEpt>
 __device__ __forceinline__ void fwd_stage(const FastPlan& p, int s, int lw, const Src& src, const Dst& dst, int tid,
                                           int nthreads) {
-  if (R <= 8 && lw >= 1) {
+  if (R <= 8 && lw >= 1 && 2 * R <= EPT) {   // pairs of columns: 2R elements per butterfly task
     fwd_stage_pairs<R, DIR, Src, Dst, EPT>(p, s, lw, src, dst, tid, nthreads);
     return;
   }
@@ -327,7 +327,7 @@ __device__ __forceinline__ void fwd_stage(const FastPlan& p, int s, int lw, cons
 template <int R, int DIR, class Src, class Dst, int EPT = kEpt>
 __device__ __forceinline__ void tr_stage(const FastPlan& p, int s, int lw, const Src& src, const Dst& dst, int tid,
                                          int nthreads) {
-  if (R <= 8 && lw >= 1) {
+  if (R <= 8 && lw >= 1 && 2 * R <= EPT) {   // pairs of columns: 2R elements per butterfly task
     tr_stage_pairs<R, DIR, Src, Dst, EPT>(p, s, lw, src, dst, tid, nthreads);
     return;
   }
@@ -691,7 +691,7 @@ __device__ __forceinline__ void green_body(const FastPlan& p, int lw, const floa
 // staging buffer S; after stage 0 has consumed S the copy of the next tile is issued, so the HBM
 // reads of tile i+1 overlap the shared-memory stages and the global stores of tile i.
 // =============================================================================================
-constexpr int kPipeEpt = 16;             // complex elements per thread per stage
+constexpr int kPipeEpt = 16;             // complex elements per thread per stage (default; 8 also built)
 constexpr int kPipeThreads = 768;
 
 __device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc, int bytes) {
@@ -744,8 +744,9 @@ template <int MAXR>
 void fast_green_launch(const fftk::FastPlan& fp, int lw, dim3 grid, int threads, size_t smem, const float2* in,
                        float2* const out[3], int pc, int nc, const float* dtab, float g_scale, cudaStream_t st);
 template <int MAXR>
-void pipe_pencils_launch(const fftk::FastPlan& fp, int lw, int ctas, int threads, size_t smem, int dir, float2* data,
-                         long long jstride, long long ostride, int nc, int nchunks, int ntiles, cudaStream_t st);
+void pipe_pencils_launch(const fftk::FastPlan& fp, int lw, int ctas, int threads, size_t smem, int dir, int ept,
+                         float2* data, long long jstride, long long ostride, int nc, int nchunks, int ntiles,
+                         cudaStream_t st);
 void generic_r2c_launch(const FftDev& d, int lw, unsigned blocks, int threads, size_t smem, int kind, const void* src,
                         long long rs, float scale, float2* dst, int pc, long long nrows, unsigned long long* acc,
                         cudaStream_t st);

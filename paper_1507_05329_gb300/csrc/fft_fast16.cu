@@ -1,4 +1,4 @@
-// Row, pencil and pipelined FFT kernels for plans whose largest radix is 16.
+// Row and pencil FFT kernels for plans whose largest radix is 16.
 #define COLA_MAXR 16
 #define COLA_PART_MAIN 1
 #define COLA_PART_GREEN 0

@@ -110,8 +110,10 @@ def test_ic_2lpt(npd, nm, box):
 
 
 # ---- S1-S5 one step on identical float32 inputs --------------------------------------------
-@pytest.mark.parametrize("i", [1, 5, 10])
-def test_single_step(i):
+@pytest.mark.parametrize("i,sched", [(1, None), (5, None), (10, None), (5, 7), (5, 23), (10, 23)])
+def test_single_step(i, sched):
+    """One step against the oracle, under the default schedule and with the tile-wise kick-drift
+    gather (7: one CTA per tile; 23: persistent CTAs staging the next tile meanwhile)."""
     npd, nm = 32, 64
     wn = cola_inputs.white_noise(npd, seed=1)
     op = oparams(**SMALL)
@@ -121,6 +123,8 @@ def test_single_step(i):
     v = rng.normal(0, 0.05, r1.shape).astype(np.float32)
     p1, p2 = r1.astype(np.float32), r2.astype(np.float32)
     ctx = ctx_for(**SMALL)
+    if sched is not None:
+        ctx.schedule = sched
     sg, vg = dev(s), dev(v)
     ctx.step(i, sg, vg, dev(p1), dev(p2))
     ctx.sync()
@@ -182,6 +186,26 @@ def test_run_is_bit_reproducible():
     ctx.sync()
     for key in ("s", "v", "pk"):
         assert torch.equal(a[key], b[key]), key
+
+
+@pytest.mark.parametrize("npd,nm,pipelined", [(32, 64, False), (32, 32, False), (24, 48, False), (32, 64, True),
+                                               (24, 48, True)])
+def test_run_equals_a_loop_of_steps(npd, nm, pipelined):
+    """cola_run is bit-identical to cola_ic_2lpt, separate cola_step calls and cola_power_spectrum,
+    with the tile-wise kick-drift gather (one CTA per tile, or persistent CTAs)."""
+    from paper_1507_05329_gb300 import binding
+    wn = dev(cola_inputs.white_noise(npd, seed=7))
+    ctx = ctx_for(np_side=npd, nmesh=nm, box=100.0)
+    # the tile-wise gather, selected even where tiles are sparse
+    ctx.schedule = (binding.SCHED_BINNED_DEPOSIT | binding.SCHED_TILE_GATHER | binding.SCHED_PIPELINED_FFT
+                    | (binding.SCHED_PIPELINED_GATHER if pipelined else 0))
+    run = ctx.run(wn, nbins=16)
+    s, v, p1, p2 = ctx.ic_2lpt(wn)
+    for i in range(1, 11):
+        ctx.step(i, s, v, p1, p2)
+    pk = ctx.power_spectrum(s, 16)
+    ctx.sync()
+    assert torch.equal(run["s"], s) and torch.equal(run["v"], v) and torch.equal(run["pk"], pk)
 
 
 @pytest.mark.parametrize("kw", [dict(ic_mode=1), dict(drift_ansatz=1), dict(nstep=4), dict(nmesh=16)])
