@@ -84,3 +84,12 @@ def plane_wave_directions(np_side: int, count: int, seed: int, mmax: int) -> np.
         ph = rng.uniform(0.0, 2.0 * np.pi)
         out[i] = np.cos(2.0 * np.pi * (m[0] * qx + m[1] * qy + m[2] * qz) / np_side + ph).ravel()
     return out
+
+
+def random_displacements_torch(np_side: int, seed: int, amplitude: float, device):
+    """float32 [3, n] Gaussian displacements (mesh cells) drawn on the device by torch's seeded
+    generator (full-size tests, where drawing 3 x 10^9 values on the host is slow)."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    return torch.randn((3, np_side ** 3), generator=g, device=device, dtype=torch.float32) * amplitude
