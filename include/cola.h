@@ -149,6 +149,10 @@ int cola_power_spectrum(cola_ctx* ctx, const float* s, double* pk, int nbins);
  *   COLA_SCHED_PIPELINED_GATHER: the tile gather runs on persistent CTAs that copy the next tile's
  *                               forces while interpolating the current one (requires
  *                               COLA_SCHED_TILE_GATHER).
+ *   COLA_SCHED_GREEN_EPT8     : the fused x + Green + inverse-x pass gives each thread 8 complex values
+ *                               per stage instead of 16 (narrower tiles, fewer registers per thread).
+ *   COLA_SCHED_ROWS_EPT8      : the same for the contiguous-axis passes (R2C of the density, C2R of the
+ *                               forces).
  *   bits COLA_SCHED_BUDGET_SHIFT..+1 : shared-memory budget per CTA of the pipelined passes,
  *                               0: 160 KB, 1: 96 KB, 2: 64 KB (sets their tile width); must be 0
  *                               without COLA_SCHED_PIPELINED_FFT.
@@ -156,19 +160,24 @@ int cola_power_spectrum(cola_ctx* ctx, const float* s, double* pk, int nbins);
  * replaces it (COLA_ERR_INVALID for an unavailable or malformed schedule).
  * cola_autotune times `reps` PM force evaluations (deposit, FFTs, Poisson + gradient, gather) at
  * displacements s (device float32 [3][np^3]; an evolved state is representative, a lattice is not)
- * for every valid schedule, keeps the fastest and writes it to *best (may be NULL), and the
- * per-candidate milliseconds, in increasing schedule order, to ms[0..max_candidates) (may be NULL).
- * Returns the number of candidates, or minus a cola_status.  It synchronises the stream and
- * allocates a temporary force array: call it outside graph capture. */
+ * in a coordinate search from the current schedule: the deposit/gather choice, then the strided
+ * passes (pipelining, elements per thread, budget), then the Green pass, then the row passes, each
+ * with the others fixed.  It keeps the fastest, writes it to *best (may be NULL), and writes the
+ * schedules it timed and their milliseconds per evaluation, in timing order, to
+ * scheds[0..max_candidates) and ms[0..max_candidates) (either may be NULL).  Returns the number of
+ * schedules timed, or minus a cola_status.  It synchronises the stream and allocates a temporary
+ * force array: call it outside graph capture. */
 #define COLA_SCHED_BINNED_DEPOSIT 1
 #define COLA_SCHED_TILE_GATHER 2
 #define COLA_SCHED_PIPELINED_FFT 4
 #define COLA_SCHED_PIPE_EPT8 8
 #define COLA_SCHED_PIPELINED_GATHER 16
+#define COLA_SCHED_GREEN_EPT8 32
+#define COLA_SCHED_ROWS_EPT8 64
 #define COLA_SCHED_BUDGET_SHIFT 8
 int cola_get_schedule(cola_ctx* ctx, int* schedule);
 int cola_set_schedule(cola_ctx* ctx, int schedule);
-int cola_autotune(cola_ctx* ctx, const float* s, int reps, int* best, double* ms, int max_candidates);
+int cola_autotune(cola_ctx* ctx, const float* s, int reps, int* best, int* scheds, double* ms, int max_candidates);
 
 /* ---- Reverse mode (not in the paper: the transpose of its forward model) ------------------
  * The forward being differentiated is cola_run's: 2LPT (§2.1, §2.3), then n_step COLA steps

@@ -86,7 +86,7 @@ SIGNATURES = {
     "cola_fof": ([_VP, _VP, _D, _I, _VP, _VP, _VP, _VP, _VP, _I, _VP], _I),
     "cola_get_schedule": ([_VP, ctypes.POINTER(_I)], _I),
     "cola_set_schedule": ([_VP, _I], _I),
-    "cola_autotune": ([_VP, _VP, _I, ctypes.POINTER(_I), ctypes.POINTER(_D), _I], _I),
+    "cola_autotune": ([_VP, _VP, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_D), _I], _I),
     "cola_batch_create": ([ctypes.POINTER(CParams), _VP, _I, _I, _I, _VP, ctypes.POINTER(_VP)], _I),
     "cola_batch_run": ([_VP, _I], _I),
     "cola_batch_sync": ([_VP], _I),
@@ -101,6 +101,8 @@ SCHED_TILE_GATHER = 2
 SCHED_PIPELINED_FFT = 4
 SCHED_PIPE_EPT8 = 8
 SCHED_PIPELINED_GATHER = 16
+SCHED_GREEN_EPT8 = 32
+SCHED_ROWS_EPT8 = 64
 SCHED_BUDGET_SHIFT = 8
 
 
@@ -369,14 +371,15 @@ class Context:
         _check(self.lib.cola_set_schedule(self._ptr, int(value)), "cola_set_schedule")
 
     def autotune(self, s, reps: int = 3):
-        """cola_autotune at displacements s: returns (best schedule, {schedule: ms})."""
+        """cola_autotune at displacements s: returns (best schedule, {timed schedule: ms})."""
         best = ctypes.c_int()
-        ms = (ctypes.c_double * 64)()
-        r = self.lib.cola_autotune(self._ptr, self._particles(s), int(reps), ctypes.byref(best), ms, 64)
+        cap = 256
+        sch = (ctypes.c_int * cap)()
+        ms = (ctypes.c_double * cap)()
+        r = self.lib.cola_autotune(self._ptr, self._particles(s), int(reps), ctypes.byref(best), sch, ms, cap)
         if r < 0:
             raise ColaError(-r, "cola_autotune")
-        cands = [sc for sc in range(4 << SCHED_BUDGET_SHIFT) if self._schedule_ok(sc)]
-        return best.value, {sc: ms[i] for i, sc in enumerate(cands[:r])}
+        return best.value, {sch[i]: ms[i] for i in range(min(r, cap))}
 
     def _schedule_ok(self, sc: int) -> bool:
         keep = self.schedule

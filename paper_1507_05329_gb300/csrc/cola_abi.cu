@@ -534,12 +534,14 @@ int schedule_of(const cola_ctx* c) {
   while (k < 2 && kPipeBudgetsKb[k] != c->mplan.pipe_kb) ++k;
   return (c->binned ? COLA_SCHED_BINNED_DEPOSIT : 0) | (c->tile_gather ? COLA_SCHED_TILE_GATHER : 0) |
          (c->mplan.pipe ? COLA_SCHED_PIPELINED_FFT : 0) | (c->mplan.pipe_ept == 8 ? COLA_SCHED_PIPE_EPT8 : 0) |
-         (c->gather_pipe ? COLA_SCHED_PIPELINED_GATHER : 0) | (k << COLA_SCHED_BUDGET_SHIFT);
+         (c->gather_pipe ? COLA_SCHED_PIPELINED_GATHER : 0) | (c->mplan.green_ept == 8 ? COLA_SCHED_GREEN_EPT8 : 0) |
+         (c->mplan.row_ept == 8 ? COLA_SCHED_ROWS_EPT8 : 0) | (k << COLA_SCHED_BUDGET_SHIFT);
 }
 
 bool schedule_valid(const cola_ctx* c, int sc) {
   if (sc & ~(COLA_SCHED_BINNED_DEPOSIT | COLA_SCHED_TILE_GATHER | COLA_SCHED_PIPELINED_FFT | COLA_SCHED_PIPE_EPT8 |
-             COLA_SCHED_PIPELINED_GATHER | (3 << COLA_SCHED_BUDGET_SHIFT)))
+             COLA_SCHED_PIPELINED_GATHER | COLA_SCHED_GREEN_EPT8 | COLA_SCHED_ROWS_EPT8 |
+             (3 << COLA_SCHED_BUDGET_SHIFT)))
     return false;
   if ((sc & COLA_SCHED_PIPELINED_GATHER) && !(sc & COLA_SCHED_TILE_GATHER)) return false;
   if ((sc & COLA_SCHED_PIPE_EPT8) && !(sc & COLA_SCHED_PIPELINED_FFT)) return false;   // unused knob
@@ -558,6 +560,8 @@ void apply_schedule(cola_ctx* c, int sc) {
   c->mplan.pipe_kb = kPipeBudgetsKb[(sc >> COLA_SCHED_BUDGET_SHIFT) & 3];
   c->mplan.pipe_ept = (sc & COLA_SCHED_PIPE_EPT8) ? 8 : 16;
   c->gather_pipe = (sc & COLA_SCHED_PIPELINED_GATHER) != 0;
+  c->mplan.green_ept = (sc & COLA_SCHED_GREEN_EPT8) ? 8 : 16;
+  c->mplan.row_ept = (sc & COLA_SCHED_ROWS_EPT8) ? 8 : 16;
 }
 }  // namespace
 
@@ -573,12 +577,10 @@ extern "C" int cola_set_schedule(cola_ctx* c, int schedule) {
   return COLA_OK;
 }
 
-extern "C" int cola_autotune(cola_ctx* c, const float* s, int reps, int* best, double* ms, int max_candidates) {
+extern "C" int cola_autotune(cola_ctx* c, const float* s, int reps, int* best, int* scheds, double* ms,
+                             int max_candidates) {
   if (!c || reps < 1 || max_candidates < 0) return -COLA_ERR_INVALID;
   if (check_ptr(s) != COLA_OK) return -COLA_ERR_INVALID;
-  std::vector<int> cand;
-  for (int sc = 0; sc < (4 << COLA_SCHED_BUDGET_SHIFT); ++sc)
-    if (schedule_valid(c, sc)) cand.push_back(sc);
   const int keep = schedule_of(c);
   float* force = nullptr;
   if (cuda_status(cudaMalloc(&force, (size_t)3 * c->pg.npart * sizeof(float)), "cudaMalloc tune") != COLA_OK)
@@ -589,10 +591,12 @@ extern "C" int cola_autotune(cola_ctx* c, const float* s, int reps, int* best, d
   const bool prof = c->prof;
   c->prof = false;
   const double fs = 1.5 * c->p.omega_m;   // force at a = 1
-  int st = COLA_OK, arg = -1;
-  float tbest = 0.0f;
-  for (size_t i = 0; i < cand.size() && st == COLA_OK; ++i) {
-    apply_schedule(c, cand[i]);
+  int st = COLA_OK;
+  std::vector<std::pair<int, float>> timed;   // schedule, ms per force evaluation
+  auto time_of = [&](int sc) -> float {
+    for (const auto& t : timed)
+      if (t.first == sc) return t.second;
+    apply_schedule(c, sc);
     st = force_mesh(c, s, fs);   // warm-up (lazy kernel attributes, caches)
     if (st == COLA_OK) st = gather(c, s, force, nullptr, nullptr, nullptr, nullptr, nullptr);
     cudaEventRecord(e0, c->stream);
@@ -605,11 +609,35 @@ extern "C" int cola_autotune(cola_ctx* c, const float* s, int reps, int* best, d
     float t = 0.0f;
     if (st == COLA_OK) cudaEventElapsedTime(&t, e0, e1);
     t /= reps;
-    if ((int)i < max_candidates && ms) ms[i] = t;
-    if (st == COLA_OK && (arg < 0 || t < tbest)) {
-      arg = (int)i;
-      tbest = t;
+    timed.push_back({sc, t});
+    return t;
+  };
+  // coordinate search from the current schedule: one group of knobs at a time, the others fixed
+  const int kB1 = 1 << COLA_SCHED_BUDGET_SHIFT, kB2 = 2 << COLA_SCHED_BUDGET_SHIFT;
+  const int P = COLA_SCHED_PIPELINED_FFT, E = COLA_SCHED_PIPE_EPT8;
+  const std::vector<std::pair<int, std::vector<int>>> groups = {
+      {COLA_SCHED_BINNED_DEPOSIT | COLA_SCHED_TILE_GATHER | COLA_SCHED_PIPELINED_GATHER,
+       {0, COLA_SCHED_BINNED_DEPOSIT, COLA_SCHED_BINNED_DEPOSIT | COLA_SCHED_TILE_GATHER,
+        COLA_SCHED_BINNED_DEPOSIT | COLA_SCHED_TILE_GATHER | COLA_SCHED_PIPELINED_GATHER}},
+      {P | E | (3 << COLA_SCHED_BUDGET_SHIFT), {0, P, P | E, P | kB1, P | kB1 | E, P | kB2, P | kB2 | E}},
+      {COLA_SCHED_GREEN_EPT8, {0, COLA_SCHED_GREEN_EPT8}},
+      {COLA_SCHED_ROWS_EPT8, {0, COLA_SCHED_ROWS_EPT8}}};
+  int cur = keep;
+  for (const auto& g : groups) {
+    int arg = -1;
+    float tbest = 0.0f;
+    for (int opt : g.second) {
+      const int sc = (cur & ~g.first) | opt;
+      if (!schedule_valid(c, sc)) continue;
+      const float t = time_of(sc);
+      if (st != COLA_OK) break;
+      if (arg < 0 || t < tbest) {
+        arg = sc;
+        tbest = t;
+      }
     }
+    if (st != COLA_OK) break;
+    if (arg >= 0) cur = arg;
   }
   c->prof = prof;
   cudaEventDestroy(e0);
@@ -619,9 +647,13 @@ extern "C" int cola_autotune(cola_ctx* c, const float* s, int reps, int* best, d
     apply_schedule(c, keep);
     return -st;
   }
-  apply_schedule(c, cand[arg]);
-  if (best) *best = cand[arg];
-  return (int)cand.size();
+  apply_schedule(c, cur);
+  if (best) *best = cur;
+  for (size_t i = 0; i < timed.size() && (int)i < max_candidates; ++i) {
+    if (scheds) scheds[i] = timed[i].first;
+    if (ms) ms[i] = timed[i].second;
+  }
+  return (int)timed.size();
 }
 
 // ---- friends-of-friends ------------------------------------------------------------------------

@@ -204,7 +204,7 @@ extern "C" int cola_batch_tune(cola_batch* b, int reps) {
     for (auto& t : tuned)
       if (t.first == key) sc = t.second;
     if (sc < 0) {
-      const int r = cola_autotune(c, b->io[i].s, reps, &sc, nullptr, 0);
+      const int r = cola_autotune(c, b->io[i].s, reps, &sc, nullptr, nullptr, 0);
       if (r < 0) return -r;
       tuned.push_back({key, sc});
     } else {

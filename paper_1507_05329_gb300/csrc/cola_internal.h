@@ -57,6 +57,8 @@ struct FftPlan {
   bool pipe = true;
   int pipe_kb = 160;
   int pipe_ept = 16;      // complex elements per thread of the pipelined passes (16 or 8)
+  int green_ept = 16;     // complex elements per thread of the Green pass (16 or 8)
+  int row_ept = 16;       // complex elements per thread of the row (R2C / C2R) passes (16 or 8)
 };
 
 // Factor n into radices {16, 8, 5, 4, 3, 2}; returns false if n has another prime factor.

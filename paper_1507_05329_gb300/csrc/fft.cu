@@ -166,19 +166,34 @@ void fft_plan_free(FftPlan* plan) {
   plan->tw = nullptr;
 }
 
+// Row tiles with 8 elements per thread hold at most kTileElems / 2 elements (384 threads).
+TileShape row_shape(const FftPlan& p, const Grid3& g, int nbuf) {
+  if (p.row_ept == 8 && g.n <= kTileElems / 2) {
+    TileShape t = fast_shape(g.n, largest_pow2_le(kTileElems / 2 / g.n), nbuf);
+    const int th = ((g.n << t.lw) + 7) / 8;
+    t.threads = ((th + 31) / 32) * 32;
+    return t;
+  }
+  return fast_shape(g.n, 1 << 20, nbuf);
+}
+
 int launch_r2c_rows(const FftPlan& p, const Grid3& g, RowSource kind, const void* src,
                     long long src_row_stride, float scale, float2* dst, cudaStream_t st,
                     unsigned long long* mass_acc) {
   const long long nrows = (long long)g.rows();
   FastPlan fp;
   if (fast_plan(p, &fp)) {
-    const TileShape t = fast_shape(g.n, 1 << 20, fp.nst >= 2 ? 2 : 1);
+    const TileShape t = row_shape(p, g, fp.nst >= 2 ? 2 : 1);
+    const bool e8 = p.row_ept == 8 && g.n <= kTileElems / 2;
     const unsigned blocks = (unsigned)((nrows + (2LL << t.lw) - 1) / (2LL << t.lw));
     unsigned long long* acc = kind == kSrcFixedPoint ? mass_acc : nullptr;
-    if (max_radix(fp) > 8)
-      fast_r2c_launch<16>(fp, t.lw, blocks, t.threads, t.smem, kind, src, src_row_stride, scale, dst, g.pc, nrows, acc, st);
-    else
-      fast_r2c_launch<8>(fp, t.lw, blocks, t.threads, t.smem, kind, src, src_row_stride, scale, dst, g.pc, nrows, acc, st);
+    if (max_radix(fp) > 8) {
+      if (e8) fast_r2c_launch<16, 8>(fp, t.lw, blocks, t.threads, t.smem, kind, src, src_row_stride, scale, dst, g.pc, nrows, acc, st);
+      else fast_r2c_launch<16, 16>(fp, t.lw, blocks, t.threads, t.smem, kind, src, src_row_stride, scale, dst, g.pc, nrows, acc, st);
+    } else {
+      if (e8) fast_r2c_launch<8, 8>(fp, t.lw, blocks, t.threads, t.smem, kind, src, src_row_stride, scale, dst, g.pc, nrows, acc, st);
+      else fast_r2c_launch<8, 16>(fp, t.lw, blocks, t.threads, t.smem, kind, src, src_row_stride, scale, dst, g.pc, nrows, acc, st);
+    }
     return check_launch("r2c_fast");
   }
   const TileShape t = tile_shape(g.n, 1 << 20);
@@ -192,10 +207,16 @@ int launch_c2r_rows(const FftPlan& p, const Grid3& g, float2* data, cudaStream_t
   const long long nrows = (long long)g.rows();
   FastPlan fp;
   if (fast_plan(p, &fp)) {
-    const TileShape t = fast_shape(g.n, 1 << 20, fp.nst >= 3 ? 2 : 1);
+    const TileShape t = row_shape(p, g, fp.nst >= 3 ? 2 : 1);
+    const bool e8 = p.row_ept == 8 && g.n <= kTileElems / 2;
     const unsigned blocks = (unsigned)((nrows + (2LL << t.lw) - 1) / (2LL << t.lw));
-    if (max_radix(fp) > 8) fast_c2r_launch<16>(fp, t.lw, blocks, t.threads, t.smem, data, g.pc, nrows, st);
-    else fast_c2r_launch<8>(fp, t.lw, blocks, t.threads, t.smem, data, g.pc, nrows, st);
+    if (max_radix(fp) > 8) {
+      if (e8) fast_c2r_launch<16, 8>(fp, t.lw, blocks, t.threads, t.smem, data, g.pc, nrows, st);
+      else fast_c2r_launch<16, 16>(fp, t.lw, blocks, t.threads, t.smem, data, g.pc, nrows, st);
+    } else {
+      if (e8) fast_c2r_launch<8, 8>(fp, t.lw, blocks, t.threads, t.smem, data, g.pc, nrows, st);
+      else fast_c2r_launch<8, 16>(fp, t.lw, blocks, t.threads, t.smem, data, g.pc, nrows, st);
+    }
     return check_launch("c2r_fast");
   }
   const TileShape t = tile_shape(g.n, 1 << 20);
@@ -241,12 +262,26 @@ int launch_green_x(const FftPlan& p, const Grid3& g, const float2* in, float2* c
   const float g_scale = (float)((double)scale / (kf * kf * n3));
   FastPlan fp;
   if (fast_plan(p, &fp)) {
+    if (p.green_ept == 8 && g.n <= kTileElems / 2) {
+      // half the elements per thread: tiles of at most 3072 elements keep 384 threads
+      const TileShape t = fast_shape(g.n, largest_pow2_le(g.nc) < kTileElems / 2 / g.n ?
+                                          largest_pow2_le(g.nc) : largest_pow2_le(kTileElems / 2 / g.n),
+                                     fp.nst >= 3 ? 2 : 1);
+      int th = ((g.n << t.lw) + 7) / 8;
+      th = ((th + 31) / 32) * 32;
+      dim3 grid((g.nc + (1 << t.lw) - 1) >> t.lw, g.n);
+      if (max_radix(fp) > 8)
+        fast_green_launch<16, 8>(fp, t.lw, grid, th, t.smem, in, out, g.pc, g.nc, dtab, g_scale, st);
+      else
+        fast_green_launch<8, 8>(fp, t.lw, grid, th, t.smem, in, out, g.pc, g.nc, dtab, g_scale, st);
+      return check_launch("green_fast8");
+    }
     const TileShape t = fast_shape(g.n, largest_pow2_le(g.nc), fp.nst >= 3 ? 2 : 1);
     dim3 grid((g.nc + (1 << t.lw) - 1) >> t.lw, g.n);
     if (max_radix(fp) > 8)
-      fast_green_launch<16>(fp, t.lw, grid, t.threads, t.smem, in, out, g.pc, g.nc, dtab, g_scale, st);
+      fast_green_launch<16, 16>(fp, t.lw, grid, t.threads, t.smem, in, out, g.pc, g.nc, dtab, g_scale, st);
     else
-      fast_green_launch<8>(fp, t.lw, grid, t.threads, t.smem, in, out, g.pc, g.nc, dtab, g_scale, st);
+      fast_green_launch<8, 16>(fp, t.lw, grid, t.threads, t.smem, in, out, g.pc, g.nc, dtab, g_scale, st);
     return check_launch("green_fast");
   }
   const TileShape t = tile_shape(g.n, largest_pow2_le(g.nc));

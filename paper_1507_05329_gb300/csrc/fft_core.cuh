@@ -410,45 +410,45 @@ struct SmemW {
 
 // Forward transform of a tile: stage 0 reads gsrc, the last stage writes gdst, shared memory
 // (buffers a, b) in between.  Ends with a barrier only when the caller asks (sync_end).
-template <int DIR, int MAXR, class GSrc, class GDst>
+template <int DIR, int MAXR, class GSrc, class GDst, int EPT = kEpt>
 __device__ __forceinline__ void fwd_tile(const FastPlan& p, int lw, float2* a, float2* b, const GSrc& gsrc,
                                          const GDst& gdst, int tid, int nt) {
   const int m = p.nst;
   if (m == 1) {
-    any_stage<false, DIR, MAXR>(p, 0, lw, gsrc, gdst, tid, nt);
+    any_stage_e<false, DIR, MAXR, EPT>(p, 0, lw, gsrc, gdst, tid, nt);
     return;
   }
-  any_stage<false, DIR, MAXR>(p, 0, lw, gsrc, SmemW{a, lw}, tid, nt);
+  any_stage_e<false, DIR, MAXR, EPT>(p, 0, lw, gsrc, SmemW{a, lw}, tid, nt);
   __syncthreads();
   for (int s = 1; s < m - 1; ++s) {
-    any_stage<false, DIR, MAXR>(p, s, lw, SmemR{a, lw}, SmemW{b, lw}, tid, nt);
+    any_stage_e<false, DIR, MAXR, EPT>(p, s, lw, SmemR{a, lw}, SmemW{b, lw}, tid, nt);
     __syncthreads();
     float2* t = a;
     a = b;
     b = t;
   }
-  any_stage<false, DIR, MAXR>(p, m - 1, lw, SmemR{a, lw}, gdst, tid, nt);
+  any_stage_e<false, DIR, MAXR, EPT>(p, m - 1, lw, SmemR{a, lw}, gdst, tid, nt);
 }
 
 // Inverse transform of a tile by the transposed stages m-1 .. 0.
-template <int DIR, int MAXR, class GSrc, class GDst>
+template <int DIR, int MAXR, class GSrc, class GDst, int EPT = kEpt>
 __device__ __forceinline__ void inv_tile(const FastPlan& p, int lw, float2* a, float2* b, const GSrc& gsrc,
                                          const GDst& gdst, int tid, int nt) {
   const int m = p.nst;
   if (m == 1) {
-    any_stage<true, DIR, MAXR>(p, 0, lw, gsrc, gdst, tid, nt);
+    any_stage_e<true, DIR, MAXR, EPT>(p, 0, lw, gsrc, gdst, tid, nt);
     return;
   }
-  any_stage<true, DIR, MAXR>(p, m - 1, lw, gsrc, SmemW{a, lw}, tid, nt);
+  any_stage_e<true, DIR, MAXR, EPT>(p, m - 1, lw, gsrc, SmemW{a, lw}, tid, nt);
   __syncthreads();
   for (int s = m - 2; s > 0; --s) {
-    any_stage<true, DIR, MAXR>(p, s, lw, SmemR{a, lw}, SmemW{b, lw}, tid, nt);
+    any_stage_e<true, DIR, MAXR, EPT>(p, s, lw, SmemR{a, lw}, SmemW{b, lw}, tid, nt);
     __syncthreads();
     float2* t = a;
     a = b;
     b = t;
   }
-  any_stage<true, DIR, MAXR>(p, 0, lw, SmemR{a, lw}, gdst, tid, nt);
+  any_stage_e<true, DIR, MAXR, EPT>(p, 0, lw, SmemR{a, lw}, gdst, tid, nt);
 }
 
 // ---- global-memory views ---------------------------------------------------------------------
@@ -569,10 +569,10 @@ struct PencilG2 {
 
 // Inverse x transform of the register-resident spectrum (times i D_x(k_x) when GRADX) into gout:
 // the transposed last stage straight from registers, then the remaining stages in shared memory.
-template <int RL, int MAXR, bool GRADX, class GDst>
-__device__ __forceinline__ void green_inverse(const FastPlan& p, int lw, const float2 (&spec)[(kEpt + RL - 1) / RL][RL],
+template <int RL, int MAXR, int EPT, bool GRADX, class GDst>
+__device__ __forceinline__ void green_inverse(const FastPlan& p, int lw, const float2 (&spec)[(EPT + RL - 1) / RL][RL],
                                               const float* __restrict__ dtab, const GDst& gout, float2* a, float2* b) {
-  constexpr int kB = (kEpt + RL - 1) / RL;
+  constexpr int kB = (EPT + RL - 1) / RL;
   const int n = p.n, tid = threadIdx.x, nt = blockDim.x, m = p.nst;
   const int nb = n / RL, total = nb << lw, wm = (1 << lw) - 1;
   const int ls = p.lns[m - 1], tstr = p.tstr[m - 1];
@@ -609,25 +609,26 @@ __device__ __forceinline__ void green_inverse(const FastPlan& p, int lw, const f
   if (m > 1) {
     __syncthreads();
     for (int s = m - 2; s > 0; --s) {
-      any_stage<true, +1, MAXR>(p, s, lw, SmemR{cur, lw}, SmemW{nxt, lw}, tid, nt);
+      any_stage_e<true, +1, MAXR, EPT>(p, s, lw, SmemR{cur, lw}, SmemW{nxt, lw}, tid, nt);
       __syncthreads();
       float2* t = cur;
       cur = nxt;
       nxt = t;
     }
-    any_stage<true, +1, MAXR>(p, 0, lw, SmemR{cur, lw}, gout, tid, nt);
+    any_stage_e<true, +1, MAXR, EPT>(p, 0, lw, SmemR{cur, lw}, gout, tid, nt);
     __syncthreads();   // before the next inverse reuses the buffers
   }
 }
 
 // x pass fused with Green function and gradient kernel, spectrum kept in registers between the
-// forward transform's last stage and the inverse transforms' first (transposed) stage.
-template <int RL, int MAXR>
+// forward transform's last stage and the inverse transforms' first (transposed) stage.  EPT:
+// complex elements per thread per stage (16, or 8: twice the threads, half the registers held).
+template <int RL, int MAXR, int EPT>
 __device__ __forceinline__ void green_body(const FastPlan& p, int lw, const float2* in, float2* out0, float2* out1,
                                            float2* out2, int pc, int nc, const float* __restrict__ dtab,
                                            float g_scale) {
   extern __shared__ float2 sm[];
-  constexpr int kB = (kEpt + RL - 1) / RL;
+  constexpr int kB = (EPT + RL - 1) / RL;
   const int n = p.n, tid = threadIdx.x, nt = blockDim.x, m = p.nst;
   const int col0 = blockIdx.x << lw, y = blockIdx.y;
   const long long jstride = (long long)n * pc;
@@ -641,10 +642,10 @@ __device__ __forceinline__ void green_body(const FastPlan& p, int lw, const floa
   // forward stages 0 .. m-2 (shared memory), last stage into registers
   const float2* last_in = nullptr;
   if (m > 1) {
-    any_stage<false, -1, MAXR>(p, 0, lw, gin, SmemW{a, lw}, tid, nt);
+    any_stage_e<false, -1, MAXR, EPT>(p, 0, lw, gin, SmemW{a, lw}, tid, nt);
     __syncthreads();
     for (int s = 1; s < m - 1; ++s) {
-      any_stage<false, -1, MAXR>(p, s, lw, SmemR{a, lw}, SmemW{b, lw}, tid, nt);
+      any_stage_e<false, -1, MAXR, EPT>(p, s, lw, SmemR{a, lw}, SmemW{b, lw}, tid, nt);
       __syncthreads();
       float2* t = a;
       a = b;
@@ -678,11 +679,11 @@ __device__ __forceinline__ void green_body(const FastPlan& p, int lw, const floa
   __syncthreads();   // the forward's shared buffers are free from here on
   // D_y(k_y) and D_z(k_z) are constant along an x pencil, so F_y and F_z are i D_y H and i D_z H of
   // one inverse H = IFFT_x(g delta): two inverse transforms instead of three
-  green_inverse<RL, MAXR, true>(p, lw, spec, dtab, PencilG{out0 + boff, jstride, nc - col0}, sm,
-                                sm + fast_tile_elems(n, lw));
-  green_inverse<RL, MAXR, false>(p, lw, spec, dtab,
-                                 PencilG2{out1 + boff, out2 + boff, jstride, nc - col0, dtab[y], dtab + col0}, sm,
-                                 sm + fast_tile_elems(n, lw));
+  green_inverse<RL, MAXR, EPT, true>(p, lw, spec, dtab, PencilG{out0 + boff, jstride, nc - col0}, sm,
+                                     sm + fast_tile_elems(n, lw));
+  green_inverse<RL, MAXR, EPT, false>(p, lw, spec, dtab,
+                                      PencilG2{out1 + boff, out2 + boff, jstride, nc - col0, dtab[y], dtab + col0}, sm,
+                                      sm + fast_tile_elems(n, lw));
 }
 
 // =============================================================================================
@@ -730,17 +731,17 @@ inline void ensure_smem(K kernel) {
 }  // namespace fftk
 
 // Launchers of the kernels compiled in the separate FFT translation units.
-template <int MAXR>
+template <int MAXR, int EPT>
 void fast_r2c_launch(const fftk::FastPlan& fp, int lw, unsigned blocks, int threads, size_t smem, int kind,
                      const void* src, long long rs, float scale, float2* dst, int pc, long long nrows,
                      unsigned long long* acc, cudaStream_t st);
-template <int MAXR>
+template <int MAXR, int EPT>
 void fast_c2r_launch(const fftk::FastPlan& fp, int lw, unsigned blocks, int threads, size_t smem, float2* data, int pc,
                      long long nrows, cudaStream_t st);
 template <int MAXR>
 void fast_pencils_launch(const fftk::FastPlan& fp, int lw, dim3 grid, int threads, size_t smem, int dir, float2* data,
                          long long jstride, long long ostride, int nc, cudaStream_t st);
-template <int MAXR>
+template <int MAXR, int EPT>
 void fast_green_launch(const fftk::FastPlan& fp, int lw, dim3 grid, int threads, size_t smem, const float2* in,
                        float2* const out[3], int pc, int nc, const float* dtab, float g_scale, cudaStream_t st);
 template <int MAXR>
