@@ -62,6 +62,8 @@ __device__ __forceinline__ void unpack_q(unsigned e, int np, int* q, long long* 
   *id = ((long long)q[0] * np + q[1]) * np + q[2];
 }
 
+constexpr int kGatherEnt = 1024;   // entries staged in shared memory per tile (4 KB)
+
 // Exact 64-bit shared-memory add from two native 32-bit atomics (low word with carry out).
 __device__ __forceinline__ void smem_add64(unsigned long long* p, unsigned long long w) {
   unsigned* h = reinterpret_cast<unsigned*>(p);
@@ -311,6 +313,12 @@ struct GatherTile {
   int x0, y0, z0;
 };
 
+// floats of one tile's staged forces: 3 components x (T+1)^2 rows of hp
+__host__ __device__ __forceinline__ int gather_floats(const BinGeom& b) {
+  const int hx = (1 << b.lt) + 1, hp = ((1 << b.lz) + 1 + 3) & ~3;
+  return 3 * hx * hx * hp;
+}
+
 __device__ __forceinline__ GatherTile gather_tile_origin(const BinGeom& b, int tile) {
   const int bz = tile % b.nz, bxy = tile / b.nz;
   const int bx = bxy / b.nt, by = bxy - bx * b.nt;
@@ -352,7 +360,8 @@ __device__ __forceinline__ void gather_stage(float* fsm, const BinGeom& b, int n
 template <bool KICK>
 __device__ __forceinline__ bool gather_particles(const float* fsm, const ParticleGeom& pg, const BinGeom& b,
                                                  const GatherTile& t, unsigned e0, unsigned e1,
-                                                 const unsigned* __restrict__ ent_p, const float* __restrict__ s_in,
+                                                 const unsigned* __restrict__ ent_p, const unsigned* ent_s,
+                                                 unsigned ne, const float* __restrict__ s_in,
                                                  float* __restrict__ force_out, float* s, float* v,
                                                  const float* __restrict__ psi1, const float* __restrict__ psi2,
                                                  const KickDrift& kd) {
@@ -365,7 +374,7 @@ __device__ __forceinline__ bool gather_particles(const float* fsm, const Particl
   for (unsigned e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
     int q[3];
     long long id;
-    unpack_q(ent_p[e], pg.np, q, &id);
+    unpack_q(e - e0 < ne ? ent_s[e - e0] : ent_p[e], pg.np, q, &id);
     const float* sp = KICK ? s : s_in;
     float sv[3], pv1[3], pv2[3], vv[3];
     if (KICK) {
@@ -437,10 +446,18 @@ __global__ void __launch_bounds__(kThreads) k_gather_tiles(ParticleGeom pg, BinG
   const unsigned e0 = off_p[tile], e1 = off_p[tile + 1];
   if (e0 == e1) return;                          // empty (uniform across the block)
   const GatherTile t = gather_tile_origin(b, tile);
+  // the tile's first kGatherEnt entries travel with the forces: one dependent global load fewer
+  unsigned* ent_s = reinterpret_cast<unsigned*>(fsm + gather_floats(b));
+  const unsigned ne = e1 - e0 < (unsigned)kGatherEnt ? e1 - e0 : (unsigned)kGatherEnt;
+  for (unsigned i = threadIdx.x; i < ne; i += blockDim.x) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(ent_s + i);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(ent_p + e0 + i) : "memory");
+  }
   gather_stage(fsm, b, pg.n, t, f0, f1, f2, rs);
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
   __syncthreads();
-  const bool bad = gather_particles<KICK>(fsm, pg, b, t, e0, e1, ent_p, s_in, force_out, s, v, psi1, psi2, kd);
+  const bool bad = gather_particles<KICK>(fsm, pg, b, t, e0, e1, ent_p, ent_s, ne, s_in, force_out, s, v, psi1, psi2,
+                                          kd);
   if (KICK && __syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flags, 2);
 }
 
@@ -477,8 +494,8 @@ __global__ void __launch_bounds__(kThreads) k_gather_tiles_pipe(ParticleGeom pg,
     __syncthreads();   // tile t staged; every thread is done with the other buffer
     const int tn = next_tile(t + gridDim.x);
     if (tn < ntiles) gather_stage(bnext, b, pg.n, gather_tile_origin(b, tn), f0, f1, f2, rs);
-    bad |= gather_particles<KICK>(bcur, pg, b, gather_tile_origin(b, t), off_p[t], off_p[t + 1], ent_p, s_in,
-                                  force_out, s, v, psi1, psi2, kd);
+    bad |= gather_particles<KICK>(bcur, pg, b, gather_tile_origin(b, t), off_p[t], off_p[t + 1], ent_p, nullptr, 0u,
+                                  s_in, force_out, s, v, psi1, psi2, kd);
     float* tmp = bcur;
     bcur = bnext;
     bnext = tmp;
@@ -579,6 +596,7 @@ int launch_gather_tiles(const ParticleGeom& pg, const BinGeom& b, const BinBuffe
                         long long rs, const float* s_in, float* force_out, float* s, float* v, const float* psi1,
                         const float* psi2, const KickDrift* kd, int* flags, cudaStream_t st, bool pipelined) {
   const size_t sm = gather_smem_bytes(b);
+  const size_t sm_ent = (size_t)gather_floats(b) * sizeof(float) + kGatherEnt * sizeof(unsigned);
   const KickDrift k = kd ? *kd : KickDrift{};
   if (pipelined) {
     // two staging buffers per CTA: as many CTAs per SM as the shared memory holds (at most 4)
@@ -598,11 +616,11 @@ int launch_gather_tiles(const ParticleGeom& pg, const BinGeom& b, const BinBuffe
     return check_launch("gather_tiles_pipe");
   }
   if (kd)
-    k_gather_tiles<true><<<b.tiles, kThreads, sm, st>>>(pg, b, bb.off_p, bb.ent_p, f[0], f[1], f[2], rs, nullptr,
-                                                         nullptr, s, v, psi1, psi2, k, flags);
+    k_gather_tiles<true><<<b.tiles, kThreads, sm_ent, st>>>(pg, b, bb.off_p, bb.ent_p, f[0], f[1], f[2], rs, nullptr,
+                                                             nullptr, s, v, psi1, psi2, k, flags);
   else
-    k_gather_tiles<false><<<b.tiles, kThreads, sm, st>>>(pg, b, bb.off_p, bb.ent_p, f[0], f[1], f[2], rs, s_in,
-                                                          force_out, nullptr, nullptr, nullptr, nullptr, k, flags);
+    k_gather_tiles<false><<<b.tiles, kThreads, sm_ent, st>>>(pg, b, bb.off_p, bb.ent_p, f[0], f[1], f[2], rs, s_in,
+                                                              force_out, nullptr, nullptr, nullptr, nullptr, k, flags);
   return check_launch("gather_tiles");
 }
 
