@@ -103,6 +103,7 @@ SCHED_PIPE_EPT8 = 8
 SCHED_PIPELINED_GATHER = 16
 SCHED_GREEN_EPT8 = 32
 SCHED_ROWS_EPT8 = 64
+SCHED_ROWS_PIPE = 128
 SCHED_BUDGET_SHIFT = 8
 
 

@@ -59,6 +59,7 @@ struct FftPlan {
   int pipe_ept = 16;      // complex elements per thread of the pipelined passes (16 or 8)
   int green_ept = 16;     // complex elements per thread of the Green pass (16 or 8)
   int row_ept = 16;       // complex elements per thread of the row (R2C / C2R) passes (16 or 8)
+  bool row_pipe = false;  // persistent C2R passes with a staging buffer for the next tile
 };
 
 // Factor n into radices {16, 8, 5, 4, 3, 2}; returns false if n has another prime factor.

@@ -206,6 +206,32 @@ int launch_r2c_rows(const FftPlan& p, const Grid3& g, RowSource kind, const void
 int launch_c2r_rows(const FftPlan& p, const Grid3& g, float2* data, cudaStream_t st) {
   const long long nrows = (long long)g.rows();
   FastPlan fp;
+  if (p.row_pipe && fast_plan(p, &fp)) {
+    // persistent CTAs: the widest tile (2W rows) with the staging copy and the stage buffers in
+    // 110 KB and at most kPipeThreads threads
+    const int ept = p.row_ept, nbuf = fp.nst >= 3 ? 2 : 1;
+    auto smem_of = [&](int lw) {
+      return ((size_t)(2 << lw) * g.pc + (size_t)nbuf * (g.n + g.n / 16 + 1) * (1u << lw)) * sizeof(float2);
+    };
+    auto threads_of = [&](int lw) { return (((g.n << lw) + ept - 1) / ept + 31) / 32 * 32; };
+    int lw = 0;
+    while ((2LL << (lw + 1)) <= nrows && smem_of(lw + 1) <= 110 * 1024 && threads_of(lw + 1) <= kPipeThreads) ++lw;
+    const int th = threads_of(lw) < 64 ? 64 : threads_of(lw);
+    if (th <= kPipeThreads && (long long)th * ept >= (long long)(g.n << lw)) {
+      const size_t smem = smem_of(lw);
+      const long long ntiles = (nrows + (2LL << lw) - 1) / (2LL << lw);
+      int dev = 0, sms = 152;
+      if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      int per_sm = (int)((227 * 1024) / (smem + 1024));
+      if (per_sm * th > 2048) per_sm = 2048 / th;
+      if (per_sm > 3) per_sm = 3;
+      if (per_sm < 1) per_sm = 1;
+      const int ctas = (int)(ntiles < (long long)sms * per_sm ? ntiles : (long long)sms * per_sm);
+      if (max_radix(fp) > 8) c2r_pipe_launch<16>(fp, lw, ctas, th, smem, ept, data, g.pc, nrows, ntiles, st);
+      else c2r_pipe_launch<8>(fp, lw, ctas, th, smem, ept, data, g.pc, nrows, ntiles, st);
+      return check_launch("c2r_pipe");
+    }
+  }
   if (fast_plan(p, &fp)) {
     const TileShape t = row_shape(p, g, fp.nst >= 3 ? 2 : 1);
     const bool e8 = p.row_ept == 8 && g.n <= kTileElems / 2;

@@ -718,6 +718,37 @@ __device__ __forceinline__ void fetch_tile(float2* S, const float2* data, long l
 }
 
 
+// Issue the copy of `rows` consecutive complex half rows (row0 ..) of stride pc into S, row-major
+// with stride pc, as 16-byte pieces (pc is even); rows past nrows are zero-filled.
+__device__ __forceinline__ void fetch_rows(float2* S, const float2* data, int pc, long long row0, long long nrows,
+                                           int rows, int tid, int nt) {
+  const int per = pc >> 1;
+  for (int q = tid; q < rows * per; q += nt) {
+    const int r = q / per, c = (q - r * per) * 2;
+    const bool ok = row0 + r < nrows;
+    cp_async16(S + (long long)r * pc + c, ok ? (const void*)(data + (row0 + r) * pc + c) : (const void*)data,
+               ok ? 16 : 0);
+  }
+  cp_async_commit();
+}
+
+// C[k] = A[k] + i B[k] of two Hermitian half rows, read from the staged copy (HalfPairSrc's
+// expansion; staged rows past nrows are zero).
+struct HalfPairS {
+  const float2* s;
+  int pc, n;
+  __device__ __forceinline__ float2 operator()(int k, int w) const {
+    const int nh = n / 2, kk = k <= nh ? k : n - k;
+    float2 A = s[(2 * w) * pc + kk], B = s[(2 * w + 1) * pc + kk];
+    if (kk == 0 || kk == nh) {
+      A.y = 0.f;
+      B.y = 0.f;
+    }
+    return k <= nh ? make_float2(A.x - B.y, A.y + B.x) : make_float2(A.x + B.y, B.x - A.y);
+  }
+  __device__ __forceinline__ float4 ld2(int k, int w) const { return pack2((*this)(k, w), (*this)(k, w + 1)); }
+};
+
 // Raises a kernel's dynamic shared-memory limit the first time it is launched (host side).
 template <class K>
 inline void ensure_smem(K kernel) {
@@ -744,6 +775,9 @@ void fast_pencils_launch(const fftk::FastPlan& fp, int lw, dim3 grid, int thread
 template <int MAXR, int EPT>
 void fast_green_launch(const fftk::FastPlan& fp, int lw, dim3 grid, int threads, size_t smem, const float2* in,
                        float2* const out[3], int pc, int nc, const float* dtab, float g_scale, cudaStream_t st);
+template <int MAXR>
+void c2r_pipe_launch(const fftk::FastPlan& fp, int lw, int ctas, int threads, size_t smem, int ept, float2* data, int pc,
+                     long long nrows, long long ntiles, cudaStream_t st);
 template <int MAXR>
 void pipe_pencils_launch(const fftk::FastPlan& fp, int lw, int ctas, int threads, size_t smem, int dir, int ept,
                          float2* data, long long jstride, long long ostride, int nc, int nchunks, int ntiles,

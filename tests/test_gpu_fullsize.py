@@ -63,7 +63,7 @@ def fixed_cells(s, ids):
     return g >> 20, ((g >> 6) & 16383).double() / 16384.0
 
 
-SCHEDULES = [None, 15, 31, 47, 79]   # default; 8-element pipelined passes; + pipelined gather; + 8-element Green; + 8-element rows
+SCHEDULES = [None, 15, 31, 47, 79, 143]   # default; 8-element pipelined passes; + pipelined gather; + 8-element Green; + 8-element rows; + pipelined C2R
 
 
 @pytest.mark.parametrize("sched", SCHEDULES)
