@@ -121,6 +121,13 @@ bool fft_factor(int n, std::vector<int>* radices) {
   while (m % 5 == 0) { m /= 5; ++n5; }
   while (m % 3 == 0) { m /= 3; ++n3; }
   if (m != 1) return false;
+  // one factor 3 and no 5: when the powers of two would need one stage more for their last factor
+  // 2 (p2 = 1 mod 4, e.g. 1536 = 8 8 8 3), that 2 joins the 3 in a last radix-6 stage (16 16 6)
+  const bool radix6 = n3 == 1 && n5 == 0 && p2 % 4 == 1;
+  if (radix6) {
+    --p2;
+    n3 = 0;
+  }
   // powers of two: the fewest stages of radix <= 16, as even as possible
   if (p2 > 0) {
     const int nst = (p2 + 3) / 4;
@@ -133,6 +140,7 @@ bool fft_factor(int n, std::vector<int>* radices) {
   }
   for (int i = 0; i < n5; ++i) radices->push_back(5);
   for (int i = 0; i < n3; ++i) radices->push_back(3);
+  if (radix6) radices->push_back(6);
   return (int)radices->size() <= kMaxStages;
 }
 

@@ -119,6 +119,26 @@ template <int DIR> struct Dft<3, DIR> {
   }
 };
 
+// 6 = 2 x 3: radix 2 first, a_j = x_j + x_{j+3} and b_j = (x_j - x_{j+3}) w6^j, then a 3-point DFT of
+// each; the even outputs come from a, the odd from b.
+template <int DIR> struct Dft<6, DIR> {
+  __device__ __forceinline__ static void run(float2* v) {
+    const float h = 0.86602540378443865f;   // sqrt(3)/2
+    float2 a[3] = {v[0] + v[3], v[1] + v[4], v[2] + v[5]};
+    float2 b[3] = {v[0] - v[3], v[1] - v[4], v[2] - v[5]};
+    b[1] = cmul(b[1], make_float2(0.5f, DIR * h));
+    b[2] = cmul(b[2], make_float2(-0.5f, DIR * h));
+    Dft<3, DIR>::run(a);
+    Dft<3, DIR>::run(b);
+    v[0] = a[0];
+    v[1] = b[0];
+    v[2] = a[1];
+    v[3] = b[1];
+    v[4] = a[2];
+    v[5] = b[2];
+  }
+};
+
 template <int DIR> struct Dft<5, DIR> {
   __device__ __forceinline__ static void run(float2* v) {
     const float c1 = 0.30901699437494742f, c2 = -0.80901699437494742f;
@@ -179,6 +199,7 @@ __device__ float2* fft_smem(float2* a, float2* b, const FftDev& p, int lw, int t
     switch (r) {
       case 16: fft_stage<16, DIR>(a, b, p.n, lw, ns, p.tw, tid, nthreads); break;
       case 8: fft_stage<8, DIR>(a, b, p.n, lw, ns, p.tw, tid, nthreads); break;
+      case 6: fft_stage<6, DIR>(a, b, p.n, lw, ns, p.tw, tid, nthreads); break;
       case 5: fft_stage<5, DIR>(a, b, p.n, lw, ns, p.tw, tid, nthreads); break;
       case 4: fft_stage<4, DIR>(a, b, p.n, lw, ns, p.tw, tid, nthreads); break;
       case 3: fft_stage<3, DIR>(a, b, p.n, lw, ns, p.tw, tid, nthreads); break;
@@ -366,6 +387,7 @@ __device__ __forceinline__ void any_stage(const FastPlan& p, int s, int lw, cons
       }
       break;
     case 8: TR ? tr_stage<8, DIR>(p, s, lw, src, dst, tid, nt) : fwd_stage<8, DIR>(p, s, lw, src, dst, tid, nt); break;
+    case 6: TR ? tr_stage<6, DIR>(p, s, lw, src, dst, tid, nt) : fwd_stage<6, DIR>(p, s, lw, src, dst, tid, nt); break;
     case 5: TR ? tr_stage<5, DIR>(p, s, lw, src, dst, tid, nt) : fwd_stage<5, DIR>(p, s, lw, src, dst, tid, nt); break;
     case 4: TR ? tr_stage<4, DIR>(p, s, lw, src, dst, tid, nt) : fwd_stage<4, DIR>(p, s, lw, src, dst, tid, nt); break;
     case 3: TR ? tr_stage<3, DIR>(p, s, lw, src, dst, tid, nt) : fwd_stage<3, DIR>(p, s, lw, src, dst, tid, nt); break;
@@ -384,6 +406,7 @@ __device__ __forceinline__ void any_stage_e(const FastPlan& p, int s, int lw, co
       }
       break;
     case 8: TR ? tr_stage<8, DIR, Src, Dst, EPT>(p, s, lw, src, dst, tid, nt) : fwd_stage<8, DIR, Src, Dst, EPT>(p, s, lw, src, dst, tid, nt); break;
+    case 6: TR ? tr_stage<6, DIR, Src, Dst, EPT>(p, s, lw, src, dst, tid, nt) : fwd_stage<6, DIR, Src, Dst, EPT>(p, s, lw, src, dst, tid, nt); break;
     case 5: TR ? tr_stage<5, DIR, Src, Dst, EPT>(p, s, lw, src, dst, tid, nt) : fwd_stage<5, DIR, Src, Dst, EPT>(p, s, lw, src, dst, tid, nt); break;
     case 4: TR ? tr_stage<4, DIR, Src, Dst, EPT>(p, s, lw, src, dst, tid, nt) : fwd_stage<4, DIR, Src, Dst, EPT>(p, s, lw, src, dst, tid, nt); break;
     case 3: TR ? tr_stage<3, DIR, Src, Dst, EPT>(p, s, lw, src, dst, tid, nt) : fwd_stage<3, DIR, Src, Dst, EPT>(p, s, lw, src, dst, tid, nt); break;

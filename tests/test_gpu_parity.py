@@ -62,7 +62,8 @@ def test_deposit_is_deterministic():
 
 
 # ---- S2 forward FFT of delta ------------------------------------------------------------------
-@pytest.mark.parametrize("npd,nm", [(16, 32), (24, 48), (20, 40), (30, 60), (32, 64), (48, 96), (40, 80)])
+@pytest.mark.parametrize("npd,nm", [(16, 32), (24, 48), (20, 40), (30, 60), (32, 64), (48, 96), (40, 80), (6, 6),
+                                    (96, 96)])
 def test_density_spectrum(npd, nm):
     s = cola_inputs.random_displacements(npd, seed=nm, amplitude=2.0)
     ctx = ctx_for(np_side=npd, nmesh=nm, box=100.0)
@@ -77,7 +78,8 @@ def test_density_spectrum(npd, nm):
 
 # ---- S1-S3 force at particles -----------------------------------------------------------------
 @pytest.mark.parametrize("npd,nm,a", [(16, 32, 0.3), (32, 64, 1.0), (24, 48, 0.5), (20, 40, 0.7),
-                                      (32, 32, 0.6), (48, 48, 0.9), (64, 64, 0.4)])
+                                      (32, 32, 0.6), (48, 48, 0.9), (64, 64, 0.4), (48, 96, 0.8), (96, 96, 0.5),
+                                      (6, 6, 0.7)])
 def test_pm_force(npd, nm, a):
     # r = 1 cases are dense enough to take the tile-wise gather from shared memory
     s = cola_inputs.random_displacements(npd, seed=7 * nm, amplitude=1.5)
@@ -93,7 +95,8 @@ def test_pm_force(npd, nm, a):
 
 
 # ---- S0 2LPT ---------------------------------------------------------------------------------
-@pytest.mark.parametrize("npd,nm,box", [(16, 32, 128.0), (32, 64, 256.0), (24, 48, 200.0), (20, 40, 150.0)])
+@pytest.mark.parametrize("npd,nm,box", [(16, 32, 128.0), (32, 64, 256.0), (24, 48, 200.0), (20, 40, 150.0),
+                                        (96, 96, 300.0), (6, 12, 60.0)])
 def test_ic_2lpt(npd, nm, box):
     wn = cola_inputs.white_noise(npd, seed=npd)
     ctx = ctx_for(np_side=npd, nmesh=nm, box=box)
