@@ -112,35 +112,61 @@ __global__ void __launch_bounds__(kThreads) k_bin(ParticleGeom pg, BinGeom b, co
   const long long modulus = (long long)pg.n << kFracBits;
   const int np = pg.np;
   const long long nrows = (long long)np * np;
-  for (long long row = blockIdx.x; row < nrows; row += gridDim.x) {
+  // the block walks (row, chunk) pairs; the positions of the next pair are loaded before this
+  // pair's atomics, so the two latencies overlap
+  const int nch = (np + (int)blockDim.x - 1) / (int)blockDim.x;
+  long long row = blockIdx.x;
+  int ch = 0;
+  float p0 = 0.f, p1 = 0.f, p2 = 0.f;
+  auto load = [&](long long r, int c, float& a0, float& a1, float& a2) {
+    const int qz = c * (int)blockDim.x + (int)threadIdx.x;
+    if (qz < np) {
+      const long long id = r * np + qz;
+      a0 = __ldg(s + id);
+      a1 = __ldg(s + n + id);
+      a2 = __ldg(s + 2 * n + id);
+    }
+  };
+  if (row < nrows) load(row, 0, p0, p1, p2);
+  while (row < nrows) {
+    long long nrow = row;
+    int nchk = ch + 1;
+    if (nchk == nch) {
+      nchk = 0;
+      nrow += gridDim.x;
+    }
+    float n0 = 0.f, n1 = 0.f, n2 = 0.f;
+    if (nrow < nrows) load(nrow, nchk, n0, n1, n2);
     const int qx = (int)(row / np), qy = (int)(row - (long long)qx * np);
     // whole warps walk the row together so that the warp-aggregated atomics see full warps
-    for (int qz0 = 0; qz0 < np; qz0 += blockDim.x) {
-      const int qz = qz0 + threadIdx.x;
-      const bool live = qz < np;
-      const long long id = row * np + qz;
-      int k[8] = {-1, -1, -1, -1, -1, -1, -1, -1};
-      if (live) {
-        const int cx = (int)(fixed_coord(qx, __ldg(s + id), pg.r_fixed, modulus) >> kFracBits);
-        const int cy = (int)(fixed_coord(qy, __ldg(s + n + id), pg.r_fixed, modulus) >> kFracBits);
-        const int cz = (int)(fixed_coord(qz, __ldg(s + 2 * n + id), pg.r_fixed, modulus) >> kFracBits);
-        tile_keys(b, cx, cy, cz, k);
-      }
-      const unsigned packed = pack_q(qx, qy, qz);
-      if (__any_sync(__activemask(), live)) {
-        // primary keys are shared by runs of lanes: one aggregated atomic per run
-        const unsigned slot = agg_inc(cnt_p, k[0], SCATTER);
-        if (SCATTER && k[0] >= 0) ent_p[slot] = packed;
-      }
-      // spill keys are sparse: one atomic per entry
+    const int qz = ch * (int)blockDim.x + (int)threadIdx.x;
+    const bool live = qz < np;
+    int k[8] = {-1, -1, -1, -1, -1, -1, -1, -1};
+    if (live) {
+      const int cx = (int)(fixed_coord(qx, p0, pg.r_fixed, modulus) >> kFracBits);
+      const int cy = (int)(fixed_coord(qy, p1, pg.r_fixed, modulus) >> kFracBits);
+      const int cz = (int)(fixed_coord(qz, p2, pg.r_fixed, modulus) >> kFracBits);
+      tile_keys(b, cx, cy, cz, k);
+    }
+    const unsigned packed = pack_q(qx, qy, qz);
+    if (__any_sync(__activemask(), live)) {
+      // primary keys are shared by runs of lanes: one aggregated atomic per run
+      const unsigned slot = agg_inc(cnt_p, k[0], SCATTER);
+      if (SCATTER && k[0] >= 0) ent_p[slot] = packed;
+    }
+    // spill keys are sparse: one atomic per entry
 #pragma unroll
-      for (int e = 1; e < 8; ++e) {
-        if (k[e] >= 0) {
-          const unsigned sl = atomicAdd(cnt_s + k[e], 1u);
-          if (SCATTER) ent_s[sl] = packed;
-        }
+    for (int e = 1; e < 8; ++e) {
+      if (k[e] >= 0) {
+        const unsigned sl = atomicAdd(cnt_s + k[e], 1u);
+        if (SCATTER) ent_s[sl] = packed;
       }
     }
+    row = nrow;
+    ch = nchk;
+    p0 = n0;
+    p1 = n1;
+    p2 = n2;
   }
 }
 
