@@ -5,7 +5,8 @@
 //   S0 cola_ic_2lpt ........ white noise -> delta_L -> Psi1, Psi2 (§2.1, §2.3)
 //   S1 deposit ............. CIC, 64-bit fixed point (§2.3, §3.3)
 //   S2 forward FFT ......... z (R2C, fused fixed-point -> delta), y
-//   S3 Poisson + gradient .. x forward fused with -1/k^2, the 4-point gradient and inverse x (x3);
+//   S3 Poisson + gradient .. x forward fused with -1/k^2, the 4-point gradient and inverse x (F_x;
+//                            F_y and F_z from one shared transform);
 //                            then inverse y and C2R z for each component (§2.2 Poisson equation)
 //   S4+S5 gather/kick/drift  CIC interpolation + eqs. (cola-kick), (cola-drift) (§2.1, §2.2)
 //   S6 power spectrum ...... §3.3

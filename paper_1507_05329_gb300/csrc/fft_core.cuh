@@ -8,7 +8,8 @@
 //   * strided axes (y, x): W adjacent complex columns per tile, so each row segment is a
 //     contiguous W*8-byte run;
 //   * the last forward pass (x) is fused with the Poisson Green function, the 4-point gradient
-//     kernel and the three inverse x transforms of the force components (§2.2 Poisson equation).
+//     kernel and the inverse x transforms of the force components (§2.2 Poisson equation): F_x
+//     has its own, F_y and F_z share one (their gradient factors are constant along x).
 // Shared-memory layout of a tile: element (j, w) at ((j + j/16) * W + w); the skew of one W-row
 // every 16 rows keeps the stride-R writes of the first Stockham stages off a single bank group.
 #pragma once
