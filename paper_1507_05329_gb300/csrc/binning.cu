@@ -396,13 +396,23 @@ __device__ __forceinline__ bool gather_particles(const float* fsm, const Particl
   const long long modulus = (long long)pg.n << kFracBits;
   const float inv_one = 1.0f / kWeightOne;
   bool bad = false;
-#pragma unroll 2
+  const float* sp = KICK ? s : s_in;
+  // rolling prefetch: the next particle's entry and position are loaded while this one is
+  // interpolated
+  int qn[3] = {0, 0, 0};
+  long long idn = 0;
+  float sn[3] = {0.f, 0.f, 0.f};
+  auto fetch = [&](unsigned e) {
+    unpack_q(e - e0 < ne ? ent_s[e - e0] : ent_p[e], pg.np, qn, &idn);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) sn[a] = sp[a * n + idn];
+  };
+  if (e0 + threadIdx.x < e1) fetch(e0 + threadIdx.x);
   for (unsigned e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-    int q[3];
-    long long id;
-    unpack_q(e - e0 < ne ? ent_s[e - e0] : ent_p[e], pg.np, q, &id);
-    const float* sp = KICK ? s : s_in;
-    float sv[3], pv1[3], pv2[3], vv[3];
+    const int q[3] = {qn[0], qn[1], qn[2]};
+    const long long id = idn;
+    float sv[3] = {sn[0], sn[1], sn[2]};
+    float pv1[3], pv2[3], vv[3];
     if (KICK) {
       // issue every particle load up front: their latency overlaps the interpolation below
 #pragma unroll
@@ -412,11 +422,11 @@ __device__ __forceinline__ bool gather_particles(const float* fsm, const Particl
         vv[a] = v[a * n + id];
       }
     }
+    if (e + blockDim.x < e1) fetch(e + blockDim.x);
     int c[3];
     float w1[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      sv[a] = sp[a * n + id];
       const long long g = fixed_coord(q[a], sv[a], pg.r_fixed, modulus);
       c[a] = (int)(g >> kFracBits);
       w1[a] = (float)((int)(g >> (kFracBits - 14)) & (kWeightOne - 1)) * inv_one;
