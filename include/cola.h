@@ -151,20 +151,21 @@ int cola_power_spectrum(cola_ctx* ctx, const float* s, double* pk, int nbins);
  *                               COLA_SCHED_TILE_GATHER).
  *   COLA_SCHED_GREEN_EPT8     : the fused x + Green + inverse-x pass gives each thread 8 complex values
  *                               per stage instead of 16 (narrower tiles, fewer registers per thread).
- *   COLA_SCHED_ROWS_EPT8      : the same for the contiguous-axis passes (R2C of the density, C2R of the
- *                               forces).
+ *   COLA_SCHED_C2R_EPT8       : the same for the contiguous-axis C2R passes of the three forces.
  *   COLA_SCHED_ROWS_PIPE      : the C2R passes run on persistent CTAs that copy the next tile's rows
  *                               (cp.async) while transforming the current one.
  *   bits COLA_SCHED_BUDGET_SHIFT..+1 : shared-memory budget per CTA of the pipelined passes,
  *                               0: 160 KB, 1: 96 KB, 2: 64 KB (sets their tile width); must be 0
  *                               without COLA_SCHED_PIPELINED_FFT.
+ *   COLA_SCHED_R2C_EPT8       : 8 complex values per thread per stage in the contiguous-axis R2C
+ *                               pass of the density.
  * cola_create picks a schedule from the sizes; cola_get_schedule reads it and cola_set_schedule
  * replaces it (COLA_ERR_INVALID for an unavailable or malformed schedule).
  * cola_autotune times `reps` PM force evaluations (deposit, FFTs, Poisson + gradient, gather) at
  * displacements s (device float32 [3][np^3]; an evolved state is representative, a lattice is not)
  * in a coordinate search from the current schedule: the deposit/gather choice, then the strided
- * passes (pipelining, elements per thread, budget), then the Green pass, then the row passes
- * (elements per thread, pipelined C2R), each
+ * passes (pipelining, elements per thread, budget), then the Green pass, then the C2R passes
+ * (elements per thread, pipelining), then the R2C pass, each
  * with the others fixed.  It keeps the fastest, writes it to *best (may be NULL), and writes the
  * schedules it timed and their milliseconds per evaluation, in timing order, to
  * scheds[0..max_candidates) and ms[0..max_candidates) (either may be NULL).  Returns the number of
@@ -176,9 +177,10 @@ int cola_power_spectrum(cola_ctx* ctx, const float* s, double* pk, int nbins);
 #define COLA_SCHED_PIPE_EPT8 8
 #define COLA_SCHED_PIPELINED_GATHER 16
 #define COLA_SCHED_GREEN_EPT8 32
-#define COLA_SCHED_ROWS_EPT8 64
+#define COLA_SCHED_C2R_EPT8 64
 #define COLA_SCHED_ROWS_PIPE 128
 #define COLA_SCHED_BUDGET_SHIFT 8
+#define COLA_SCHED_R2C_EPT8 1024
 int cola_get_schedule(cola_ctx* ctx, int* schedule);
 int cola_set_schedule(cola_ctx* ctx, int schedule);
 int cola_autotune(cola_ctx* ctx, const float* s, int reps, int* best, int* scheds, double* ms, int max_candidates);

@@ -102,9 +102,10 @@ SCHED_PIPELINED_FFT = 4
 SCHED_PIPE_EPT8 = 8
 SCHED_PIPELINED_GATHER = 16
 SCHED_GREEN_EPT8 = 32
-SCHED_ROWS_EPT8 = 64
+SCHED_C2R_EPT8 = 64
 SCHED_ROWS_PIPE = 128
 SCHED_BUDGET_SHIFT = 8
+SCHED_R2C_EPT8 = 1024
 
 
 class BatchIO(ctypes.Structure):

@@ -58,7 +58,8 @@ struct FftPlan {
   int pipe_kb = 160;
   int pipe_ept = 16;      // complex elements per thread of the pipelined passes (16 or 8)
   int green_ept = 16;     // complex elements per thread of the Green pass (16 or 8)
-  int row_ept = 16;       // complex elements per thread of the row (R2C / C2R) passes (16 or 8)
+  int row_ept = 16;       // complex elements per thread of the C2R row passes (16 or 8)
+  int r2c_ept = 16;       // complex elements per thread of the R2C row pass (16 or 8)
   bool row_pipe = false;  // persistent C2R passes with a staging buffer for the next tile
 };
 

@@ -74,6 +74,21 @@ int max_radix(const FastPlan& fp) {
   return m;
 }
 
+// Row index of a shared tile with one padding row per 16 (the device's saddr without the column).
+int padded_row(int j) { return j + (j >> 4); }
+
+// Padded step along stride d for the butterflies of a radix-R stage whose first rows are `starts`:
+// the step that every row j0 + r d (r < R) of every butterfly lands on, or 0 when the padding is not
+// affine along d.  Checked row by row, so a plan never takes the fixed-step addressing unless it
+// gives exactly the rows saddr gives.
+int affine_step(const std::vector<int>& starts, int d, int R) {
+  const int step = padded_row(starts[0] + d) - padded_row(starts[0]);
+  for (int j0 : starts)
+    for (int r = 0; r < R; ++r)
+      if (padded_row(j0 + r * d) != padded_row(j0) + r * step) return 0;
+  return step;
+}
+
 // Fast path eligibility: every stage's ns is a power of two.
 bool fast_plan(const FftPlan& pl, FastPlan* fp) {
   const FftDev& d = pl.dev;
@@ -85,12 +100,22 @@ bool fast_plan(const FftPlan& pl, FastPlan* fp) {
     if (ns & (ns - 1)) return false;
     int l = 0;
     while ((1 << l) < ns) ++l;
-    fp->radix[s] = d.radix[s];
+    const int R = d.radix[s], nb = d.n / R;
+    fp->radix[s] = R;
     fp->lns[s] = l;
-    fp->tstr[s] = d.n / (ns * d.radix[s]);
-    ns *= d.radix[s];
+    fp->tstr[s] = d.n / (ns * R);
+    // butterfly b < nb touches rows b + r nb and ((b >> l) R << l) + (b mod ns) + r ns
+    std::vector<int> by_nb(nb), by_ns(nb);
+    for (int b = 0; b < nb; ++b) {
+      by_nb[b] = b;
+      by_ns[b] = (((b >> l) * R) << l) + (b & (ns - 1));
+    }
+    fp->nbp[s] = affine_step(by_nb, nb, R);
+    fp->nsp[s] = affine_step(by_ns, ns, R);
+    ns *= R;
   }
-  for (int s = d.nstages; s < kMaxStages; ++s) fp->radix[s] = 1, fp->lns[s] = 0, fp->tstr[s] = 0;
+  for (int s = d.nstages; s < kMaxStages; ++s)
+    fp->radix[s] = 1, fp->lns[s] = 0, fp->tstr[s] = 0, fp->nbp[s] = 0, fp->nsp[s] = 0;
   return true;
 }
 
@@ -175,8 +200,8 @@ void fft_plan_free(FftPlan* plan) {
 }
 
 // Row tiles with 8 elements per thread hold at most kTileElems / 2 elements (384 threads).
-TileShape row_shape(const FftPlan& p, const Grid3& g, int nbuf) {
-  if (p.row_ept == 8 && g.n <= kTileElems / 2) {
+TileShape row_shape(int ept, const Grid3& g, int nbuf) {
+  if (ept == 8 && g.n <= kTileElems / 2) {
     TileShape t = fast_shape(g.n, largest_pow2_le(kTileElems / 2 / g.n), nbuf);
     const int th = ((g.n << t.lw) + 7) / 8;
     t.threads = ((th + 31) / 32) * 32;
@@ -191,8 +216,8 @@ int launch_r2c_rows(const FftPlan& p, const Grid3& g, RowSource kind, const void
   const long long nrows = (long long)g.rows();
   FastPlan fp;
   if (fast_plan(p, &fp)) {
-    const TileShape t = row_shape(p, g, fp.nst >= 2 ? 2 : 1);
-    const bool e8 = p.row_ept == 8 && g.n <= kTileElems / 2;
+    const TileShape t = row_shape(p.r2c_ept, g, fp.nst >= 2 ? 2 : 1);
+    const bool e8 = p.r2c_ept == 8 && g.n <= kTileElems / 2;
     const unsigned blocks = (unsigned)((nrows + (2LL << t.lw) - 1) / (2LL << t.lw));
     unsigned long long* acc = kind == kSrcFixedPoint ? mass_acc : nullptr;
     if (max_radix(fp) > 8) {
@@ -241,7 +266,7 @@ int launch_c2r_rows(const FftPlan& p, const Grid3& g, float2* data, cudaStream_t
     }
   }
   if (fast_plan(p, &fp)) {
-    const TileShape t = row_shape(p, g, fp.nst >= 3 ? 2 : 1);
+    const TileShape t = row_shape(p.row_ept, g, fp.nst >= 3 ? 2 : 1);
     const bool e8 = p.row_ept == 8 && g.n <= kTileElems / 2;
     const unsigned blocks = (unsigned)((nrows + (2LL << t.lw) - 1) / (2LL << t.lw));
     if (max_radix(fp) > 8) {

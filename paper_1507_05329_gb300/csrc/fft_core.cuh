@@ -229,6 +229,11 @@ struct FastPlan {
   int radix[kMaxStages];
   int lns[kMaxStages];    // log2 of ns at each stage
   int tstr[kMaxStages];   // twiddle stride n / (ns R)
+  // Padded row steps of a shared tile (saddr) along the stage's two strides, 0 where the padding
+  // is not affine along them: rows j0 + r n/R sit at saddr(j0) + r nbp W, rows j0 + r ns at
+  // saddr(j0) + r nsp W (checked exhaustively on the host when the plan is made).
+  int nbp[kMaxStages];
+  int nsp[kMaxStages];
   const float2* tw;
 };
 
@@ -239,10 +244,111 @@ __device__ __forceinline__ float2 twid(const float2* __restrict__ tw, int t) {
   return v;
 }
 
+struct SmemR {
+  const float2* s;
+  int lw;
+  __device__ __forceinline__ float2 operator()(int j, int w) const { return s[saddr(j, w, lw)]; }
+  __device__ __forceinline__ float4 ld2(int j, int w) const {
+    return *reinterpret_cast<const float4*>(s + saddr(j, w, lw));
+  }
+};
+struct SmemW {
+  float2* s;
+  int lw;
+  __device__ __forceinline__ void operator()(int j, int w, float2 v) const { s[saddr(j, w, lw)] = v; }
+  __device__ __forceinline__ void st2(int j, int w, float4 v) const {
+    *reinterpret_cast<float4*>(s + saddr(j, w, lw)) = v;
+  }
+};
+template <class T>
+struct SmemAcc {
+  static constexpr bool value = false;
+};
+template <>
+struct SmemAcc<SmemR> {
+  static constexpr bool value = true;
+};
+template <>
+struct SmemAcc<SmemW> {
+  static constexpr bool value = true;
+};
+
+// Rows j0 + r d (r < R) of column w.  In a shared tile whose padding is affine along d (padded
+// step dp > 0) the addresses are one pointer plus multiples of a fixed step; elsewhere each row
+// goes through the accessor.
+template <int R, class Src>
+__device__ __forceinline__ void load_rows(const Src& src, int j0, int d, int dp, int lw, int w, float2 (&v)[R]) {
+  if constexpr (SmemAcc<Src>::value) {
+    if (dp) {
+      const float2* q = src.s + saddr(j0, w, lw);
+      const int st = dp << lw;
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[r] = q[r * st];
+      return;
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r) v[r] = src(j0 + r * d, w);
+}
+template <int R, class Dst>
+__device__ __forceinline__ void store_rows(const Dst& dst, int j0, int d, int dp, int lw, int w, const float2 (&v)[R]) {
+  if constexpr (SmemAcc<Dst>::value) {
+    if (dp) {
+      float2* q = dst.s + saddr(j0, w, lw);
+      const int st = dp << lw;
+#pragma unroll
+      for (int r = 0; r < R; ++r) q[r * st] = v[r];
+      return;
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r) dst(j0 + r * d, w, v[r]);
+}
+
 // Pencil pairs: with two or more pencils per tile a thread takes the same butterfly of two
 // adjacent pencils, so the twiddles and index arithmetic are shared and every shared/global
 // access moves 16 bytes.
 __device__ __forceinline__ float4 pack2(float2 a, float2 b) { return make_float4(a.x, a.y, b.x, b.y); }
+
+// Column pairs (w, w + 1) of rows j0 + r d, as load_rows and store_rows (w even: 16-byte accesses).
+template <int R, class Src>
+__device__ __forceinline__ void load_rows2(const Src& src, int j0, int d, int dp, int lw, int w, float2 (&va)[R],
+                                           float2 (&vb)[R]) {
+  if constexpr (SmemAcc<Src>::value) {
+    if (dp) {
+      const float2* q = src.s + saddr(j0, w, lw);
+      const int st = dp << lw;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const float4 t = *reinterpret_cast<const float4*>(q + r * st);
+        va[r] = make_float2(t.x, t.y);
+        vb[r] = make_float2(t.z, t.w);
+      }
+      return;
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const float4 t = src.ld2(j0 + r * d, w);
+    va[r] = make_float2(t.x, t.y);
+    vb[r] = make_float2(t.z, t.w);
+  }
+}
+template <int R, class Dst>
+__device__ __forceinline__ void store_rows2(const Dst& dst, int j0, int d, int dp, int lw, int w, const float2 (&va)[R],
+                                            const float2 (&vb)[R]) {
+  if constexpr (SmemAcc<Dst>::value) {
+    if (dp) {
+      float2* q = dst.s + saddr(j0, w, lw);
+      const int st = dp << lw;
+#pragma unroll
+      for (int r = 0; r < R; ++r) *reinterpret_cast<float4*>(q + r * st) = pack2(va[r], vb[r]);
+      return;
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r) dst.st2(j0 + r * d, w, pack2(va[r], vb[r]));
+}
 
 template <int R, int DIR, class Src, class Dst, int EPT>
 __device__ __forceinline__ void fwd_stage_pairs(const FastPlan& p, int s, int lw, const Src& src, const Dst& dst,
@@ -256,12 +362,7 @@ __device__ __forceinline__ void fwd_stage_pairs(const FastPlan& p, int s, int lw
     if (idx < total) {
       const int w = (idx & wm) << 1, b = idx >> lwp, k = b & km;
       float2 va[R], vb[R];
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        const float4 q = src.ld2(b + r * nb, w);
-        va[r] = make_float2(q.x, q.y);
-        vb[r] = make_float2(q.z, q.w);
-      }
+      load_rows2<R>(src, b, nb, p.nbp[s], lw, w, va, vb);
       if (lns) {
 #pragma unroll
         for (int r = 1; r < R; ++r) {
@@ -273,8 +374,7 @@ __device__ __forceinline__ void fwd_stage_pairs(const FastPlan& p, int s, int lw
       Dft<R, DIR>::run(va);
       Dft<R, DIR>::run(vb);
       const int base = (((b >> lns) * R) << lns) + k;
-#pragma unroll
-      for (int r = 0; r < R; ++r) dst.st2(base + (r << lns), w, pack2(va[r], vb[r]));
+      store_rows2<R>(dst, base, 1 << lns, p.nsp[s], lw, w, va, vb);
     }
   }
 }
@@ -292,12 +392,7 @@ __device__ __forceinline__ void tr_stage_pairs(const FastPlan& p, int s, int lw,
       const int w = (idx & wm) << 1, b = idx >> lwp, k = b & km;
       const int base = (((b >> lns) * R) << lns) + k;
       float2 va[R], vb[R];
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        const float4 q = src.ld2(base + (r << lns), w);
-        va[r] = make_float2(q.x, q.y);
-        vb[r] = make_float2(q.z, q.w);
-      }
+      load_rows2<R>(src, base, 1 << lns, p.nsp[s], lw, w, va, vb);
       Dft<R, DIR>::run(va);
       Dft<R, DIR>::run(vb);
       if (lns) {
@@ -308,8 +403,7 @@ __device__ __forceinline__ void tr_stage_pairs(const FastPlan& p, int s, int lw,
           vb[r] = cmul(vb[r], t);
         }
       }
-#pragma unroll
-      for (int r = 0; r < R; ++r) dst.st2(b + r * nb, w, pack2(va[r], vb[r]));
+      store_rows2<R>(dst, b, nb, p.nbp[s], lw, w, va, vb);
     }
   }
 }
@@ -331,16 +425,14 @@ __device__ __forceinline__ void fwd_stage(const FastPlan& p, int s, int lw, cons
     if (idx < total) {
       const int w = idx & wm, b = idx >> lw, k = b & km;
       float2 v[R];
-#pragma unroll
-      for (int r = 0; r < R; ++r) v[r] = src(b + r * nb, w);
+      load_rows<R>(src, b, nb, p.nbp[s], lw, w, v);
       if (lns) {
 #pragma unroll
         for (int r = 1; r < R; ++r) v[r] = cmul(v[r], twid<DIR>(p.tw, r * k * tstr));
       }
       Dft<R, DIR>::run(v);
       const int base = (((b >> lns) * R) << lns) + k;
-#pragma unroll
-      for (int r = 0; r < R; ++r) dst(base + (r << lns), w, v[r]);
+      store_rows<R>(dst, base, 1 << lns, p.nsp[s], lw, w, v);
     }
   }
 }
@@ -363,15 +455,13 @@ __device__ __forceinline__ void tr_stage(const FastPlan& p, int s, int lw, const
       const int w = idx & wm, b = idx >> lw, k = b & km;
       const int base = (((b >> lns) * R) << lns) + k;
       float2 v[R];
-#pragma unroll
-      for (int r = 0; r < R; ++r) v[r] = src(base + (r << lns), w);
+      load_rows<R>(src, base, 1 << lns, p.nsp[s], lw, w, v);
       Dft<R, DIR>::run(v);
       if (lns) {
 #pragma unroll
         for (int r = 1; r < R; ++r) v[r] = cmul(v[r], twid<DIR>(p.tw, r * k * tstr));
       }
-#pragma unroll
-      for (int r = 0; r < R; ++r) dst(b + r * nb, w, v[r]);
+      store_rows<R>(dst, b, nb, p.nbp[s], lw, w, v);
     }
   }
 }
@@ -415,22 +505,6 @@ __device__ __forceinline__ void any_stage_e(const FastPlan& p, int s, int lw, co
   }
 }
 
-struct SmemR {
-  const float2* s;
-  int lw;
-  __device__ __forceinline__ float2 operator()(int j, int w) const { return s[saddr(j, w, lw)]; }
-  __device__ __forceinline__ float4 ld2(int j, int w) const {
-    return *reinterpret_cast<const float4*>(s + saddr(j, w, lw));
-  }
-};
-struct SmemW {
-  float2* s;
-  int lw;
-  __device__ __forceinline__ void operator()(int j, int w, float2 v) const { s[saddr(j, w, lw)] = v; }
-  __device__ __forceinline__ void st2(int j, int w, float4 v) const {
-    *reinterpret_cast<float4*>(s + saddr(j, w, lw)) = v;
-  }
-};
 
 // Forward transform of a tile: stage 0 reads gsrc, the last stage writes gdst, shared memory
 // (buffers a, b) in between.  Ends with a barrier only when the caller asks (sync_end).
@@ -623,11 +697,8 @@ __device__ __forceinline__ void green_inverse(const FastPlan& p, int lw, const f
 #pragma unroll
         for (int r = 1; r < RL; ++r) v[r] = cmul(v[r], twid<+1>(p.tw, r * bb * tstr));
       }
-#pragma unroll
-      for (int r = 0; r < RL; ++r) {
-        if (m > 1) cur[saddr(bb + r * nb, w, lw)] = v[r];
-        else gout(bb + r * nb, w, v[r]);
-      }
+      if (m > 1) store_rows<RL>(SmemW{cur, lw}, bb, nb, p.nbp[m - 1], lw, w, v);
+      else store_rows<RL>(gout, bb, nb, 0, lw, w, v);
     }
   }
   if (m > 1) {
@@ -682,8 +753,8 @@ __device__ __forceinline__ void green_body(const FastPlan& p, int lw, const floa
     const int idx = tid + i * nt;
     if (idx < total) {
       const int w = idx & wm, bb = idx >> lw;   // last stage: bb < ns, k = bb
-#pragma unroll
-      for (int r = 0; r < RL; ++r) spec[i][r] = m > 1 ? last_in[saddr(bb + r * nb, w, lw)] : gin(bb + r * nb, w);
+      if (m > 1) load_rows<RL>(SmemR{last_in, lw}, bb, nb, p.nbp[m - 1], lw, w, spec[i]);
+      else load_rows<RL>(gin, bb, nb, 0, lw, w, spec[i]);
       if (ls) {
 #pragma unroll
         for (int r = 1; r < RL; ++r) spec[i][r] = cmul(spec[i][r], twid<-1>(p.tw, r * bb * tstr));

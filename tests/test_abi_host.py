@@ -40,6 +40,21 @@ def test_library_exports_every_declared_symbol(lib):
     assert set(names) == set(binding.SIGNATURES), "binding and header disagree"
 
 
+def test_schedule_bits_match_the_header():
+    """The binding's schedule constants are the header's COLA_SCHED_* macros, bit for bit."""
+    from paper_1507_05329_gb300 import binding
+    text = open(os.path.join(ROOT, "include", "cola.h")).read()
+    macros = dict(re.findall(r"#define COLA_SCHED_(\w+) (\d+)", text))
+    assert len(macros) >= 10
+    for name, value in macros.items():
+        assert getattr(binding, "SCHED_" + name) == int(value), name
+    bits = [int(v) for k, v in macros.items() if k != "BUDGET_SHIFT"]
+    bits.append(3 << int(macros["BUDGET_SHIFT"]))
+    for i, a in enumerate(bits):   # no two knobs share a bit
+        for b in bits[i + 1:]:
+            assert a & b == 0, (a, b)
+
+
 def test_strerror(lib):
     assert lib.cola_strerror(0) == b"ok"
     assert b"overflow" in lib.cola_strerror(4)

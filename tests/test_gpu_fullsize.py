@@ -63,7 +63,9 @@ def fixed_cells(s, ids):
     return g >> 20, ((g >> 6) & 16383).double() / 16384.0
 
 
-SCHEDULES = [None, 15, 31, 47, 79, 143]   # default; 8-element pipelined passes; + pipelined gather; + 8-element Green; + 8-element rows; + pipelined C2R
+# default; 8-element pipelined passes; + pipelined gather; + 8-element Green; + 8-element C2R; + pipelined C2R;
+# 8-element R2C
+SCHEDULES = [None, 15, 31, 47, 79, 143, 1031]
 
 
 @pytest.mark.parametrize("sched", SCHEDULES)
