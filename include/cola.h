@@ -159,13 +159,17 @@ int cola_power_spectrum(cola_ctx* ctx, const float* s, double* pk, int nbins);
  *                               without COLA_SCHED_PIPELINED_FFT.
  *   COLA_SCHED_R2C_EPT8       : 8 complex values per thread per stage in the contiguous-axis R2C
  *                               pass of the density.
+ *   COLA_SCHED_WIDE_TILES     : tiles of 8 pencils (one CTA of up to 768 threads per SM) in the
+ *                               16-element Green pass and the one-CTA-per-tile strided passes where
+ *                               the default tile is narrower (meshes of 769 to 1536 cells), so that
+ *                               every row segment moved is 64 bytes; on by default.
  * cola_create picks a schedule from the sizes; cola_get_schedule reads it and cola_set_schedule
  * replaces it (COLA_ERR_INVALID for an unavailable or malformed schedule).
  * cola_autotune times `reps` PM force evaluations (deposit, FFTs, Poisson + gradient, gather) at
  * displacements s (device float32 [3][np^3]; an evolved state is representative, a lattice is not)
  * in a coordinate search from the current schedule: the deposit/gather choice, then the strided
- * passes (pipelining, elements per thread, budget), then the Green pass, then the C2R passes
- * (elements per thread, pipelining), then the R2C pass, each
+ * passes (pipelining, elements per thread, budget), then the Green pass, then the tile width, then
+ * the C2R passes (elements per thread, pipelining), then the R2C pass, each
  * with the others fixed.  It keeps the fastest, writes it to *best (may be NULL), and writes the
  * schedules it timed and their milliseconds per evaluation, in timing order, to
  * scheds[0..max_candidates) and ms[0..max_candidates) (either may be NULL).  Returns the number of
@@ -181,6 +185,7 @@ int cola_power_spectrum(cola_ctx* ctx, const float* s, double* pk, int nbins);
 #define COLA_SCHED_ROWS_PIPE 128
 #define COLA_SCHED_BUDGET_SHIFT 8
 #define COLA_SCHED_R2C_EPT8 1024
+#define COLA_SCHED_WIDE_TILES 2048
 int cola_get_schedule(cola_ctx* ctx, int* schedule);
 int cola_set_schedule(cola_ctx* ctx, int schedule);
 int cola_autotune(cola_ctx* ctx, const float* s, int reps, int* best, int* scheds, double* ms, int max_candidates);

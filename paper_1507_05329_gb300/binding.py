@@ -106,6 +106,7 @@ SCHED_C2R_EPT8 = 64
 SCHED_ROWS_PIPE = 128
 SCHED_BUDGET_SHIFT = 8
 SCHED_R2C_EPT8 = 1024
+SCHED_WIDE_TILES = 2048
 
 
 class BatchIO(ctypes.Structure):

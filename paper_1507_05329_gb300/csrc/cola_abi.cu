@@ -537,13 +537,14 @@ int schedule_of(const cola_ctx* c) {
          (c->mplan.pipe ? COLA_SCHED_PIPELINED_FFT : 0) | (c->mplan.pipe_ept == 8 ? COLA_SCHED_PIPE_EPT8 : 0) |
          (c->gather_pipe ? COLA_SCHED_PIPELINED_GATHER : 0) | (c->mplan.green_ept == 8 ? COLA_SCHED_GREEN_EPT8 : 0) |
          (c->mplan.row_ept == 8 ? COLA_SCHED_C2R_EPT8 : 0) | (c->mplan.row_pipe ? COLA_SCHED_ROWS_PIPE : 0) |
-         (k << COLA_SCHED_BUDGET_SHIFT) | (c->mplan.r2c_ept == 8 ? COLA_SCHED_R2C_EPT8 : 0);
+         (k << COLA_SCHED_BUDGET_SHIFT) | (c->mplan.r2c_ept == 8 ? COLA_SCHED_R2C_EPT8 : 0) |
+         (c->mplan.wide ? COLA_SCHED_WIDE_TILES : 0);
 }
 
 bool schedule_valid(const cola_ctx* c, int sc) {
   if (sc & ~(COLA_SCHED_BINNED_DEPOSIT | COLA_SCHED_TILE_GATHER | COLA_SCHED_PIPELINED_FFT | COLA_SCHED_PIPE_EPT8 |
              COLA_SCHED_PIPELINED_GATHER | COLA_SCHED_GREEN_EPT8 | COLA_SCHED_C2R_EPT8 | COLA_SCHED_ROWS_PIPE |
-             (3 << COLA_SCHED_BUDGET_SHIFT) | COLA_SCHED_R2C_EPT8))
+             (3 << COLA_SCHED_BUDGET_SHIFT) | COLA_SCHED_R2C_EPT8 | COLA_SCHED_WIDE_TILES))
     return false;
   if ((sc & COLA_SCHED_PIPELINED_GATHER) && !(sc & COLA_SCHED_TILE_GATHER)) return false;
   if ((sc & COLA_SCHED_PIPE_EPT8) && !(sc & COLA_SCHED_PIPELINED_FFT)) return false;   // unused knob
@@ -565,6 +566,7 @@ void apply_schedule(cola_ctx* c, int sc) {
   c->mplan.green_ept = (sc & COLA_SCHED_GREEN_EPT8) ? 8 : 16;
   c->mplan.row_ept = (sc & COLA_SCHED_C2R_EPT8) ? 8 : 16;
   c->mplan.r2c_ept = (sc & COLA_SCHED_R2C_EPT8) ? 8 : 16;
+  c->mplan.wide = (sc & COLA_SCHED_WIDE_TILES) != 0;
   c->mplan.row_pipe = (sc & COLA_SCHED_ROWS_PIPE) != 0;
 }
 }  // namespace
@@ -625,6 +627,7 @@ extern "C" int cola_autotune(cola_ctx* c, const float* s, int reps, int* best, i
         COLA_SCHED_BINNED_DEPOSIT | COLA_SCHED_TILE_GATHER | COLA_SCHED_PIPELINED_GATHER}},
       {P | E | (3 << COLA_SCHED_BUDGET_SHIFT), {0, P, P | E, P | kB1, P | kB1 | E, P | kB2, P | kB2 | E}},
       {COLA_SCHED_GREEN_EPT8, {0, COLA_SCHED_GREEN_EPT8}},
+      {COLA_SCHED_WIDE_TILES, {0, COLA_SCHED_WIDE_TILES}},
       {COLA_SCHED_C2R_EPT8 | COLA_SCHED_ROWS_PIPE,
        {0, COLA_SCHED_C2R_EPT8, COLA_SCHED_ROWS_PIPE, COLA_SCHED_C2R_EPT8 | COLA_SCHED_ROWS_PIPE}},
       {COLA_SCHED_R2C_EPT8, {0, COLA_SCHED_R2C_EPT8}}};

@@ -61,6 +61,7 @@ struct FftPlan {
   int row_ept = 16;       // complex elements per thread of the C2R row passes (16 or 8)
   int r2c_ept = 16;       // complex elements per thread of the R2C row pass (16 or 8)
   bool row_pipe = false;  // persistent C2R passes with a staging buffer for the next tile
+  bool wide = true;       // tiles of 8 pencils in the one-CTA-per-tile strided and Green passes
 };
 
 // Factor n into radices {16, 8, 5, 4, 3, 2}; returns false if n has another prime factor.

@@ -13,6 +13,7 @@ struct TileShape {
 };
 
 constexpr int kTileElems = 6144;    // complex elements per tile (two buffers: about 100 KB of shared memory)
+constexpr int kWideElems = 12288;   // wide tiles: 8 pencils of up to 1536 (two buffers: about 200 KB)
 
 TileShape tile_shape(int n, int wmax) {
   int lw = 0;
@@ -123,6 +124,19 @@ TileShape fast_shape(int n, int wmax, int nbuf) {
   TileShape t = tile_shape(n, wmax);
   t.smem = (size_t)nbuf * (size_t)(n + n / 16 + 1) * (1u << t.lw) * sizeof(float2);
   return t;
+}
+
+// Tiles of 8 pencils for the strided passes whose default tile is narrower (n > 768): every row
+// segment a tile reads and writes is then 64 bytes (two DRAM sectors) instead of 32, at one CTA of
+// up to kWideThreads threads per SM.  Measured at n = 1536: the Green pass 41.0 -> 30.8 ms.
+TileShape wide_shape(const FftPlan& p, const Grid3& g, const TileShape& t, int nbuf) {
+  if (!p.wide || t.lw >= 3 || g.n * 8 > kWideElems || g.nc < 8) return t;
+  TileShape w;
+  w.lw = 3;
+  const int th = ((g.n << 3) + kEpt - 1) / kEpt;
+  w.threads = ((th + 31) / 32) * 32;
+  w.smem = (size_t)nbuf * (size_t)(g.n + g.n / 16 + 1) * 8 * sizeof(float2);
+  return w;
 }
 
 int check_launch(const char* what) {
@@ -300,7 +314,8 @@ int launch_pencils(const FftPlan& p, const Grid3& g, int axis, int dir, float2* 
     return check_launch("pencils_pipe");
   }
   if (fast_plan(p, &fp)) {
-    const TileShape t = fast_shape(g.n, largest_pow2_le(g.nc), fp.nst >= 3 ? 2 : 1);
+    const int nbuf = fp.nst >= 3 ? 2 : 1;
+    const TileShape t = wide_shape(p, g, fast_shape(g.n, largest_pow2_le(g.nc), nbuf), nbuf);
     dim3 grid((g.nc + (1 << t.lw) - 1) >> t.lw, g.n);
     if (max_radix(fp) > 8)
       fast_pencils_launch<16>(fp, t.lw, grid, t.threads, t.smem, dir, data, jstride, ostride, g.nc, st);
@@ -335,7 +350,8 @@ int launch_green_x(const FftPlan& p, const Grid3& g, const float2* in, float2* c
         fast_green_launch<8, 8>(fp, t.lw, grid, th, t.smem, in, out, g.pc, g.nc, dtab, g_scale, st);
       return check_launch("green_fast8");
     }
-    const TileShape t = fast_shape(g.n, largest_pow2_le(g.nc), fp.nst >= 3 ? 2 : 1);
+    const int nbuf = fp.nst >= 3 ? 2 : 1;
+    const TileShape t = wide_shape(p, g, fast_shape(g.n, largest_pow2_le(g.nc), nbuf), nbuf);
     dim3 grid((g.nc + (1 << t.lw) - 1) >> t.lw, g.n);
     if (max_radix(fp) > 8)
       fast_green_launch<16, 16>(fp, t.lw, grid, t.threads, t.smem, in, out, g.pc, g.nc, dtab, g_scale, st);

@@ -25,6 +25,7 @@ namespace fftk {
 
 constexpr int kEpt = 16;   // complex elements per thread (register staging of a stage)
 constexpr int kMaxThreads = 384;   // largest tile (6144 elements) / kEpt
+constexpr int kWideThreads = 768;  // wide tiles: 8 pencils of up to 1536 elements / kEpt
 
 __device__ __forceinline__ float2 operator+(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 operator-(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }

@@ -32,7 +32,7 @@ def dev(a):
 
 def all_schedules(ctx):
     from paper_1507_05329_gb300 import binding
-    return [sc for sc in range(2 * binding.SCHED_R2C_EPT8) if ctx._schedule_ok(sc)]
+    return [sc for sc in range(2 * binding.SCHED_WIDE_TILES) if ctx._schedule_ok(sc)]
 
 
 # ---- schedules -----------------------------------------------------------------------------

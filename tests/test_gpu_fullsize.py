@@ -63,9 +63,9 @@ def fixed_cells(s, ids):
     return g >> 20, ((g >> 6) & 16383).double() / 16384.0
 
 
-# default; 8-element pipelined passes; + pipelined gather; + 8-element Green; + 8-element C2R; + pipelined C2R;
-# 8-element R2C
-SCHEDULES = [None, 15, 31, 47, 79, 143, 1031]
+# default (wide tiles); narrow tiles with: 8-element pipelined passes; + pipelined gather; + 8-element Green;
+# + 8-element C2R; + pipelined C2R; 8-element R2C; plain strided passes, narrow and wide
+SCHEDULES = [None, 15, 31, 47, 79, 143, 1031, 3, 2051]
 
 
 @pytest.mark.parametrize("sched", SCHEDULES)
