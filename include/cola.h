@@ -163,12 +163,16 @@ int cola_power_spectrum(cola_ctx* ctx, const float* s, double* pk, int nbins);
  *                               16-element Green pass and the one-CTA-per-tile strided passes where
  *                               the default tile is narrower (meshes of 769 to 1536 cells), so that
  *                               every row segment moved is 64 bytes; on by default.
+ *   COLA_SCHED_PIPE_INPLACE   : the pipelined passes keep two tile buffers (staging and one work buffer
+ *                               that the middle stages overwrite) in up to 210 KB, which holds tiles of
+ *                               8 pencils of 1536; requires COLA_SCHED_PIPELINED_FFT, budget bits 0 and
+ *                               no COLA_SCHED_PIPE_EPT8.
  * cola_create picks a schedule from the sizes; cola_get_schedule reads it and cola_set_schedule
  * replaces it (COLA_ERR_INVALID for an unavailable or malformed schedule).
  * cola_autotune times `reps` PM force evaluations (deposit, FFTs, Poisson + gradient, gather) at
  * displacements s (device float32 [3][np^3]; an evolved state is representative, a lattice is not)
  * in a coordinate search from the current schedule: the deposit/gather choice, then the strided
- * passes (pipelining, elements per thread, budget), then the Green pass, then the tile width, then
+ * passes (pipelining, elements per thread, budget or in-place tiles), then the Green pass, then the tile width, then
  * the C2R passes (elements per thread, pipelining), then the R2C pass, each
  * with the others fixed.  It keeps the fastest, writes it to *best (may be NULL), and writes the
  * schedules it timed and their milliseconds per evaluation, in timing order, to
@@ -186,6 +190,7 @@ int cola_power_spectrum(cola_ctx* ctx, const float* s, double* pk, int nbins);
 #define COLA_SCHED_BUDGET_SHIFT 8
 #define COLA_SCHED_R2C_EPT8 1024
 #define COLA_SCHED_WIDE_TILES 2048
+#define COLA_SCHED_PIPE_INPLACE 4096
 int cola_get_schedule(cola_ctx* ctx, int* schedule);
 int cola_set_schedule(cola_ctx* ctx, int schedule);
 int cola_autotune(cola_ctx* ctx, const float* s, int reps, int* best, int* scheds, double* ms, int max_candidates);

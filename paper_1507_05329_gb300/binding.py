@@ -107,6 +107,7 @@ SCHED_ROWS_PIPE = 128
 SCHED_BUDGET_SHIFT = 8
 SCHED_R2C_EPT8 = 1024
 SCHED_WIDE_TILES = 2048
+SCHED_PIPE_INPLACE = 4096
 
 
 class BatchIO(ctypes.Structure):

@@ -538,13 +538,13 @@ int schedule_of(const cola_ctx* c) {
          (c->gather_pipe ? COLA_SCHED_PIPELINED_GATHER : 0) | (c->mplan.green_ept == 8 ? COLA_SCHED_GREEN_EPT8 : 0) |
          (c->mplan.row_ept == 8 ? COLA_SCHED_C2R_EPT8 : 0) | (c->mplan.row_pipe ? COLA_SCHED_ROWS_PIPE : 0) |
          (k << COLA_SCHED_BUDGET_SHIFT) | (c->mplan.r2c_ept == 8 ? COLA_SCHED_R2C_EPT8 : 0) |
-         (c->mplan.wide ? COLA_SCHED_WIDE_TILES : 0);
+         (c->mplan.wide ? COLA_SCHED_WIDE_TILES : 0) | (c->mplan.pipe_inplace ? COLA_SCHED_PIPE_INPLACE : 0);
 }
 
 bool schedule_valid(const cola_ctx* c, int sc) {
   if (sc & ~(COLA_SCHED_BINNED_DEPOSIT | COLA_SCHED_TILE_GATHER | COLA_SCHED_PIPELINED_FFT | COLA_SCHED_PIPE_EPT8 |
              COLA_SCHED_PIPELINED_GATHER | COLA_SCHED_GREEN_EPT8 | COLA_SCHED_C2R_EPT8 | COLA_SCHED_ROWS_PIPE |
-             (3 << COLA_SCHED_BUDGET_SHIFT) | COLA_SCHED_R2C_EPT8 | COLA_SCHED_WIDE_TILES))
+             (3 << COLA_SCHED_BUDGET_SHIFT) | COLA_SCHED_R2C_EPT8 | COLA_SCHED_WIDE_TILES | COLA_SCHED_PIPE_INPLACE))
     return false;
   if ((sc & COLA_SCHED_PIPELINED_GATHER) && !(sc & COLA_SCHED_TILE_GATHER)) return false;
   if ((sc & COLA_SCHED_PIPE_EPT8) && !(sc & COLA_SCHED_PIPELINED_FFT)) return false;   // unused knob
@@ -553,6 +553,9 @@ bool schedule_valid(const cola_ctx* c, int sc) {
   if ((sc & COLA_SCHED_TILE_GATHER) && c->bg.lz < 2) return false;   // 16-byte staging copies along z
   if (((sc >> COLA_SCHED_BUDGET_SHIFT) & 3) > 2) return false;
   if (!(sc & COLA_SCHED_PIPELINED_FFT) && ((sc >> COLA_SCHED_BUDGET_SHIFT) & 3)) return false;   // unused knob
+  if ((sc & COLA_SCHED_PIPE_INPLACE) && (!(sc & COLA_SCHED_PIPELINED_FFT) || (sc & COLA_SCHED_PIPE_EPT8) ||
+                                          ((sc >> COLA_SCHED_BUDGET_SHIFT) & 3)))
+    return false;   // its own budget, 16 elements per thread
   return true;
 }
 
@@ -567,6 +570,7 @@ void apply_schedule(cola_ctx* c, int sc) {
   c->mplan.row_ept = (sc & COLA_SCHED_C2R_EPT8) ? 8 : 16;
   c->mplan.r2c_ept = (sc & COLA_SCHED_R2C_EPT8) ? 8 : 16;
   c->mplan.wide = (sc & COLA_SCHED_WIDE_TILES) != 0;
+  c->mplan.pipe_inplace = (sc & COLA_SCHED_PIPE_INPLACE) != 0;
   c->mplan.row_pipe = (sc & COLA_SCHED_ROWS_PIPE) != 0;
 }
 }  // namespace
@@ -620,12 +624,12 @@ extern "C" int cola_autotune(cola_ctx* c, const float* s, int reps, int* best, i
   };
   // coordinate search from the current schedule: one group of knobs at a time, the others fixed
   const int kB1 = 1 << COLA_SCHED_BUDGET_SHIFT, kB2 = 2 << COLA_SCHED_BUDGET_SHIFT;
-  const int P = COLA_SCHED_PIPELINED_FFT, E = COLA_SCHED_PIPE_EPT8;
+  const int P = COLA_SCHED_PIPELINED_FFT, E = COLA_SCHED_PIPE_EPT8, I = COLA_SCHED_PIPE_INPLACE;
   const std::vector<std::pair<int, std::vector<int>>> groups = {
       {COLA_SCHED_BINNED_DEPOSIT | COLA_SCHED_TILE_GATHER | COLA_SCHED_PIPELINED_GATHER,
        {0, COLA_SCHED_BINNED_DEPOSIT, COLA_SCHED_BINNED_DEPOSIT | COLA_SCHED_TILE_GATHER,
         COLA_SCHED_BINNED_DEPOSIT | COLA_SCHED_TILE_GATHER | COLA_SCHED_PIPELINED_GATHER}},
-      {P | E | (3 << COLA_SCHED_BUDGET_SHIFT), {0, P, P | E, P | kB1, P | kB1 | E, P | kB2, P | kB2 | E}},
+      {P | E | I | (3 << COLA_SCHED_BUDGET_SHIFT), {0, P, P | E, P | kB1, P | kB1 | E, P | kB2, P | kB2 | E, P | I}},
       {COLA_SCHED_GREEN_EPT8, {0, COLA_SCHED_GREEN_EPT8}},
       {COLA_SCHED_WIDE_TILES, {0, COLA_SCHED_WIDE_TILES}},
       {COLA_SCHED_C2R_EPT8 | COLA_SCHED_ROWS_PIPE,

@@ -62,6 +62,7 @@ struct FftPlan {
   int r2c_ept = 16;       // complex elements per thread of the R2C row pass (16 or 8)
   bool row_pipe = false;  // persistent C2R passes with a staging buffer for the next tile
   bool wide = true;       // tiles of 8 pencils in the one-CTA-per-tile strided and Green passes
+  bool pipe_inplace = false;  // pipelined passes: one work buffer overwritten in place, 210 KB budget
 };
 
 // Factor n into radices {16, 8, 5, 4, 3, 2}; returns false if n has another prime factor.

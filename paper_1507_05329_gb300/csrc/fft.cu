@@ -34,21 +34,26 @@ int largest_pow2_le(int v) {
   return p;
 }
 
-// Persistent pipelined strided passes: three tile buffers (staging, ping, pong) per CTA.
+// Persistent pipelined strided passes: three tile buffers (staging, ping, pong) per CTA, or two
+// (staging and one work buffer that the middle stages overwrite) in a budget of kInplaceKb.
 struct PipeShape {
   int lw, threads, nchunks, ntiles, ctas;
   size_t smem;
 };
 
-PipeShape pipe_shape(const Grid3& g, int budget_kb, int ept) {
+constexpr int kInplaceKb = 210;   // two tiles of 8 pencils of 1536
+
+PipeShape pipe_shape(const Grid3& g, int budget_kb, int ept, bool inplace) {
   PipeShape ps;
+  const size_t nbuf = inplace ? 2 : 3;
+  if (inplace) budget_kb = kInplaceKb;
   int lw = 1;   // W >= 2: 16-byte copies
   while ((2 << lw) <= largest_pow2_le(g.nc) &&
-         (size_t)3 * (g.n + g.n / 16 + 1) * (2 << lw) * 8 <= (size_t)budget_kb * 1024 &&
+         nbuf * (g.n + g.n / 16 + 1) * (2 << lw) * 8 <= (size_t)budget_kb * 1024 &&
          ((long long)g.n * (2 << lw) + ept - 1) / ept <= kPipeThreads)
     ++lw;
   ps.lw = lw;
-  ps.smem = (size_t)3 * (g.n + g.n / 16 + 1) * (1 << lw) * sizeof(float2);
+  ps.smem = nbuf * (g.n + g.n / 16 + 1) * (1 << lw) * sizeof(float2);
   int th = ((g.n << lw) + ept - 1) / ept;
   th = ((th + 31) / 32) * 32;
   ps.threads = th < 64 ? 64 : (th > kPipeThreads ? kPipeThreads : th);
@@ -65,8 +70,8 @@ PipeShape pipe_shape(const Grid3& g, int budget_kb, int ept) {
 // The pipelined kernels need at least two columns per tile and a whole tile per thread set.
 bool pipe_ok(const FftPlan& p, const Grid3& g) {
   if (!p.pipe || g.nc < 2) return false;
-  const PipeShape ps = pipe_shape(g, p.pipe_kb, p.pipe_ept);
-  return (long long)ps.threads * p.pipe_ept >= (long long)(g.n << ps.lw) && ps.smem <= 200 * 1024;
+  const PipeShape ps = pipe_shape(g, p.pipe_kb, p.pipe_ept, p.pipe_inplace);
+  return (long long)ps.threads * p.pipe_ept >= (long long)(g.n << ps.lw) && ps.smem <= kInplaceKb * 1024;
 }
 
 int max_radix(const FastPlan& fp) {
@@ -304,13 +309,13 @@ int launch_pencils(const FftPlan& p, const Grid3& g, int axis, int dir, float2* 
   const long long ostride = axis == 1 ? plane : g.pc;
   FastPlan fp;
   if (fast_plan(p, &fp) && pipe_ok(p, g)) {
-    const PipeShape ps = pipe_shape(g, p.pipe_kb, p.pipe_ept);
+    const PipeShape ps = pipe_shape(g, p.pipe_kb, p.pipe_ept, p.pipe_inplace);
     if (max_radix(fp) > 8)
-      pipe_pencils_launch<16>(fp, ps.lw, ps.ctas, ps.threads, ps.smem, dir, p.pipe_ept, data, jstride, ostride, g.nc,
-                              ps.nchunks, ps.ntiles, st);
+      pipe_pencils_launch<16>(fp, ps.lw, ps.ctas, ps.threads, ps.smem, dir, p.pipe_ept, p.pipe_inplace, data, jstride,
+                              ostride, g.nc, ps.nchunks, ps.ntiles, st);
     else
-      pipe_pencils_launch<8>(fp, ps.lw, ps.ctas, ps.threads, ps.smem, dir, p.pipe_ept, data, jstride, ostride, g.nc,
-                             ps.nchunks, ps.ntiles, st);
+      pipe_pencils_launch<8>(fp, ps.lw, ps.ctas, ps.threads, ps.smem, dir, p.pipe_ept, p.pipe_inplace, data, jstride,
+                             ostride, g.nc, ps.nchunks, ps.ntiles, st);
     return check_launch("pencils_pipe");
   }
   if (fast_plan(p, &fp)) {

@@ -507,6 +507,79 @@ __device__ __forceinline__ void any_stage_e(const FastPlan& p, int s, int lw, co
 }
 
 
+// A stage that overwrites its input buffer: each thread reads the rows of all its butterflies into
+// registers, the block synchronises, and the results go back to the same buffer (one work buffer
+// instead of two, one barrier more).  Only middle stages, whose radix is a power of two in a fast
+// plan, so a thread's EPT = 16 values fill one register array whatever the radix; the barrier sits
+// outside the radix switch.  The caller synchronises before the next stage reads.
+template <int R, bool TR, int EPT>
+__device__ __forceinline__ void inplace_read(const FastPlan& p, int s, int lw, const float2* buf, int tid, int nt,
+                                             float2 (&v)[EPT]) {
+  constexpr int kB = EPT / R;
+  const int nb = p.n / R, total = nb << lw, lns = p.lns[s];
+  const int wm = (1 << lw) - 1, km = (1 << lns) - 1;
+  const SmemR src{buf, lw};
+#pragma unroll
+  for (int i = 0; i < kB; ++i) {
+    const int idx = tid + i * nt;
+    if (idx < total) {
+      const int w = idx & wm, b = idx >> lw, k = b & km;
+      float2 t[R];
+      if (TR) load_rows<R>(src, (((b >> lns) * R) << lns) + k, 1 << lns, p.nsp[s], lw, w, t);
+      else load_rows<R>(src, b, nb, p.nbp[s], lw, w, t);
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[i * R + r] = t[r];
+    }
+  }
+}
+
+template <int R, int DIR, bool TR, int EPT>
+__device__ __forceinline__ void inplace_write(const FastPlan& p, int s, int lw, float2* buf, int tid, int nt,
+                                              const float2 (&v)[EPT]) {
+  constexpr int kB = EPT / R;
+  const int nb = p.n / R, total = nb << lw, lns = p.lns[s], tstr = p.tstr[s];
+  const int wm = (1 << lw) - 1, km = (1 << lns) - 1;
+  const SmemW dst{buf, lw};
+#pragma unroll
+  for (int i = 0; i < kB; ++i) {
+    const int idx = tid + i * nt;
+    if (idx < total) {
+      const int w = idx & wm, b = idx >> lw, k = b & km;
+      float2 t[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) t[r] = v[i * R + r];
+      if (!TR && lns) {
+#pragma unroll
+        for (int r = 1; r < R; ++r) t[r] = cmul(t[r], twid<DIR>(p.tw, r * k * tstr));
+      }
+      Dft<R, DIR>::run(t);
+      if (TR && lns) {
+#pragma unroll
+        for (int r = 1; r < R; ++r) t[r] = cmul(t[r], twid<DIR>(p.tw, r * k * tstr));
+      }
+      if (TR) store_rows<R>(dst, b, nb, p.nbp[s], lw, w, t);
+      else store_rows<R>(dst, (((b >> lns) * R) << lns) + k, 1 << lns, p.nsp[s], lw, w, t);
+    }
+  }
+}
+
+template <bool TR, int DIR, int MAXR, int EPT>
+__device__ __forceinline__ void inplace_stage(const FastPlan& p, int s, int lw, float2* buf, int tid, int nt) {
+  static_assert(EPT == 16, "in-place stages hold 16 values per thread");
+  float2 v[EPT];
+  const int R = p.radix[s];
+  if (MAXR >= 16 && R == 16) inplace_read<(MAXR >= 16 ? 16 : 8), TR, EPT>(p, s, lw, buf, tid, nt, v);
+  else if (R == 8) inplace_read<8, TR, EPT>(p, s, lw, buf, tid, nt, v);
+  else if (R == 4) inplace_read<4, TR, EPT>(p, s, lw, buf, tid, nt, v);
+  else inplace_read<2, TR, EPT>(p, s, lw, buf, tid, nt, v);
+  __syncthreads();
+  if (MAXR >= 16 && R == 16) inplace_write<(MAXR >= 16 ? 16 : 8), DIR, TR, EPT>(p, s, lw, buf, tid, nt, v);
+  else if (R == 8) inplace_write<8, DIR, TR, EPT>(p, s, lw, buf, tid, nt, v);
+  else if (R == 4) inplace_write<4, DIR, TR, EPT>(p, s, lw, buf, tid, nt, v);
+  else inplace_write<2, DIR, TR, EPT>(p, s, lw, buf, tid, nt, v);
+}
+
+
 // Forward transform of a tile: stage 0 reads gsrc, the last stage writes gdst, shared memory
 // (buffers a, b) in between.  Ends with a barrier only when the caller asks (sync_end).
 template <int DIR, int MAXR, class GSrc, class GDst, int EPT = kEpt>
@@ -876,8 +949,8 @@ void c2r_pipe_launch(const fftk::FastPlan& fp, int lw, int ctas, int threads, si
                      long long nrows, long long ntiles, cudaStream_t st);
 template <int MAXR>
 void pipe_pencils_launch(const fftk::FastPlan& fp, int lw, int ctas, int threads, size_t smem, int dir, int ept,
-                         float2* data, long long jstride, long long ostride, int nc, int nchunks, int ntiles,
-                         cudaStream_t st);
+                         bool inplace, float2* data, long long jstride, long long ostride, int nc, int nchunks,
+                         int ntiles, cudaStream_t st);
 void generic_r2c_launch(const FftDev& d, int lw, unsigned blocks, int threads, size_t smem, int kind, const void* src,
                         long long rs, float scale, float2* dst, int pc, long long nrows, unsigned long long* acc,
                         cudaStream_t st);

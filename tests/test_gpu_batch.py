@@ -31,8 +31,15 @@ def dev(a):
 
 
 def all_schedules(ctx):
-    from paper_1507_05329_gb300 import binding
-    return [sc for sc in range(2 * binding.SCHED_WIDE_TILES) if ctx._schedule_ok(sc)]
+    """Every valid combination of the knobs below the budget bits, then each of those with the R2C
+    and tile-width knobs flipped together, and with the in-place pipelined passes where valid."""
+    from paper_1507_05329_gb300 import binding as b
+    low = [sc for sc in range(4 << b.SCHED_BUDGET_SHIFT) if ctx._schedule_ok(sc)]
+    both = b.SCHED_R2C_EPT8 | b.SCHED_WIDE_TILES
+    extra = [sc | both for sc in low] + [sc | b.SCHED_PIPE_INPLACE for sc in low
+                                         if ctx._schedule_ok(sc | b.SCHED_PIPE_INPLACE)]
+    assert all(ctx._schedule_ok(sc) for sc in extra)
+    return low + extra
 
 
 # ---- schedules -----------------------------------------------------------------------------
@@ -52,7 +59,7 @@ def test_every_schedule_deposits_bit_exactly(npd, nm, amp):
     ctx.sync()
 
 
-@pytest.mark.parametrize("npd,nm", [(32, 64), (24, 72)])
+@pytest.mark.parametrize("npd,nm", [(32, 64), (24, 72), (48, 192)])   # 192 = 8 8 3: a middle stage
 def test_every_schedule_gives_the_oracle_force(npd, nm):
     """Same bar as the single-schedule force parity: max error < 1e-5 of the largest force."""
     from paper_1507_05329_gb300 import Context, Params
@@ -71,8 +78,11 @@ def test_every_schedule_gives_the_oracle_force(npd, nm):
 def test_invalid_schedules_are_rejected():
     from paper_1507_05329_gb300 import ColaError, Context, Params, binding
     ctx = Context(Params(np_side=32, nmesh=64, box=100.0))
-    for bad in (binding.SCHED_TILE_GATHER, 1 << 12, 3 << binding.SCHED_BUDGET_SHIFT,
-                1 << binding.SCHED_BUDGET_SHIFT):   # budget without the pipelined passes
+    for bad in (binding.SCHED_TILE_GATHER, 1 << 13, 3 << binding.SCHED_BUDGET_SHIFT,
+                1 << binding.SCHED_BUDGET_SHIFT,   # budget without the pipelined passes
+                binding.SCHED_PIPE_INPLACE,        # in place without the pipelined passes
+                binding.SCHED_PIPE_INPLACE | binding.SCHED_PIPELINED_FFT | (1 << binding.SCHED_BUDGET_SHIFT),
+                binding.SCHED_PIPE_INPLACE | binding.SCHED_PIPELINED_FFT | binding.SCHED_PIPE_EPT8):
         with pytest.raises(ColaError):
             ctx.schedule = bad
 

@@ -64,8 +64,8 @@ def fixed_cells(s, ids):
 
 
 # default (wide tiles); narrow tiles with: 8-element pipelined passes; + pipelined gather; + 8-element Green;
-# + 8-element C2R; + pipelined C2R; 8-element R2C; plain strided passes, narrow and wide
-SCHEDULES = [None, 15, 31, 47, 79, 143, 1031, 3, 2051]
+# + 8-element C2R; + pipelined C2R; 8-element R2C; plain strided passes, narrow and wide; in-place pipelined passes
+SCHEDULES = [None, 15, 31, 47, 79, 143, 1031, 3, 2051, 6151]
 
 
 @pytest.mark.parametrize("sched", SCHEDULES)
