@@ -362,11 +362,14 @@ def run_ours(args):
         if ws > 1:
             dist.barrier()
 
+    tuned = None
+    if args.schedule is not None:
+        ctx.schedule = args.schedule   # fixed for every realisation, warm-up included
+        tuned = {"schedule": args.schedule, "force_eval_ms": None, "fixed": True}
     for _ in range(args.warmup):
         ctx.run(wn, args.nbins, out=out)
     ctx.sync()
-    tuned = None
-    if args.autotune:
+    if args.autotune and args.schedule is None:
         # schedule chosen on the evolved (a = 1) positions of the warm-up realisation; outside the timed region
         best, times = ctx.autotune(out["s"], reps=2)
         tuned = {"schedule": best, "force_eval_ms": {str(k): round(v, 3) for k, v in times.items()}}
@@ -522,6 +525,8 @@ def main():
     ap.add_argument("--lanes", type=int, default=8, help="streams of the batched-mocks run")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="keep the size-based default schedule instead of timing the candidates first")
+    ap.add_argument("--schedule", type=int, default=None,
+                    help="run every realisation (warm-up included) under this cola_set_schedule value, untuned")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
