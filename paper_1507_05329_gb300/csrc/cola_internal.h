@@ -49,6 +49,10 @@ struct FftDev {
 struct FftPlan {
   FftDev dev{};
   float2* tw = nullptr;   // owned device memory
+  // padded shared-tile row steps of each stage along n/R and along ns (0: padding not affine),
+  // computed once by fft_plan_init for the fast-path kernels
+  int nbp[kMaxStages] = {};
+  int nsp[kMaxStages] = {};
   int w_pencil = 8;       // pencils per CTA in the strided passes
   int w_rows = 4;         // row pairs per CTA in the contiguous (R2C / C2R) passes
   int ept = 16;           // complex elements per thread
@@ -68,6 +72,7 @@ struct FftPlan {
 // Factor n into radices {16, 8, 5, 4, 3, 2}; returns false if n has another prime factor.
 bool fft_factor(int n, std::vector<int>* radices);
 int fft_plan_init(FftPlan* plan, int n);   // allocates the twiddle table; returns cola_status
+void fft_plan_steps(FftPlan* plan);        // fills nbp / nsp from dev.n and dev.radix (host only)
 void fft_plan_free(FftPlan* plan);
 void fft_set_smem_limits();                // raise the dynamic shared-memory limit of the FFT kernels
 

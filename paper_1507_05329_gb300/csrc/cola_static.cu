@@ -110,6 +110,7 @@ extern "C" int cola_power_spectrum_noalloc(const cola_params* p, const float* s,
   plan.dev.nstages = (int)rad.size();
   for (int i = 0; i < kMaxStages; ++i) plan.dev.radix[i] = i < (int)rad.size() ? rad[i] : 1;
   plan.dev.tw = reinterpret_cast<const float2*>(base + kOffTw);
+  fft_plan_steps(&plan);
 
   Grid3 g;
   g.n = n;

@@ -106,18 +106,12 @@ bool fast_plan(const FftPlan& pl, FastPlan* fp) {
     if (ns & (ns - 1)) return false;
     int l = 0;
     while ((1 << l) < ns) ++l;
-    const int R = d.radix[s], nb = d.n / R;
+    const int R = d.radix[s];
     fp->radix[s] = R;
     fp->lns[s] = l;
     fp->tstr[s] = d.n / (ns * R);
-    // butterfly b < nb touches rows b + r nb and ((b >> l) R << l) + (b mod ns) + r ns
-    std::vector<int> by_nb(nb), by_ns(nb);
-    for (int b = 0; b < nb; ++b) {
-      by_nb[b] = b;
-      by_ns[b] = (((b >> l) * R) << l) + (b & (ns - 1));
-    }
-    fp->nbp[s] = affine_step(by_nb, nb, R);
-    fp->nsp[s] = affine_step(by_ns, ns, R);
+    fp->nbp[s] = pl.nbp[s];
+    fp->nsp[s] = pl.nsp[s];
     ns *= R;
   }
   for (int s = d.nstages; s < kMaxStages; ++s)
@@ -188,12 +182,32 @@ bool fft_factor(int n, std::vector<int>* radices) {
   return (int)radices->size() <= kMaxStages;
 }
 
+// Affine row steps of the stages with a power-of-two ns (the fast-path stages): butterfly b < n/R
+// touches rows b + r n/R and ((b >> l) R << l) + (b mod ns) + r ns, ns = 2^l.
+void fft_plan_steps(FftPlan* plan) {
+  const int n = plan->dev.n, m = plan->dev.nstages;
+  for (int s = 0; s < kMaxStages; ++s) plan->nbp[s] = plan->nsp[s] = 0;
+  for (int s = 0, ns = 1; s < m && !(ns & (ns - 1)); ns *= plan->dev.radix[s], ++s) {
+    int l = 0;
+    while ((1 << l) < ns) ++l;
+    const int R = plan->dev.radix[s], nb = n / R;
+    std::vector<int> by_nb(nb), by_ns(nb);
+    for (int b = 0; b < nb; ++b) {
+      by_nb[b] = b;
+      by_ns[b] = (((b >> l) * R) << l) + (b & (ns - 1));
+    }
+    plan->nbp[s] = affine_step(by_nb, nb, R);
+    plan->nsp[s] = affine_step(by_ns, ns, R);
+  }
+}
+
 int fft_plan_init(FftPlan* plan, int n) {
   std::vector<int> rad;
   if (!fft_factor(n, &rad)) return COLA_ERR_INVALID;
   plan->dev.n = n;
   plan->dev.nstages = (int)rad.size();
   for (int i = 0; i < kMaxStages; ++i) plan->dev.radix[i] = i < (int)rad.size() ? rad[i] : 1;
+  fft_plan_steps(plan);
   std::vector<float2> h(n);
   for (int t = 0; t < n; ++t) {
     const double ang = -2.0 * M_PI * (double)t / (double)n;
