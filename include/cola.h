@@ -167,8 +167,9 @@ int cola_power_spectrum(cola_ctx* ctx, const float* s, double* pk, int nbins);
  *                               that the middle stages overwrite) in up to 210 KB, which holds tiles of
  *                               8 pencils of 1536; requires COLA_SCHED_PIPELINED_FFT, budget bits 0 and
  *                               no COLA_SCHED_PIPE_EPT8.
- * cola_create picks a schedule from the sizes; cola_get_schedule reads it and cola_set_schedule
- * replaces it (COLA_ERR_INVALID for an unavailable or malformed schedule).
+ * cola_create picks a schedule from the sizes (in-place pipelined passes for meshes of 769 to 1536
+ * cells, the binned deposit and tile gather where the tiles are dense enough); cola_get_schedule reads
+ * it and cola_set_schedule replaces it (COLA_ERR_INVALID for an unavailable or malformed schedule).
  * cola_autotune times `reps` PM force evaluations (deposit, FFTs, Poisson + gradient, gather) at
  * displacements s (device float32 [3][np^3]; an evolved state is representative, a lattice is not)
  * in a coordinate search from the current schedule: the deposit/gather choice, then the strided

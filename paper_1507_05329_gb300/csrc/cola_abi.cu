@@ -338,6 +338,13 @@ extern "C" int cola_create(const cola_params* params, void* stream, cola_ctx** o
     c->binned = true;
     c->tile_gather = tile_gather_pays(c->bg, c->pg.npart);
   }
+  // meshes of 769 to 1536 cells: the in-place pipelined strided passes hold tiles of 8 pencils
+  // (64-byte row segments) where the three-buffer ones hold 4 (at 1536: 185.6 against 203.2 ms per
+  // PM force evaluation on 1024^3 particles)
+  {
+    const int n = params->nmesh;
+    c->mplan.pipe_inplace = n > 768 && n * 8 <= 12288;
+  }
   if ((st = cuda_status(cudaMallocHost(&c->edges_host, (kPkMaxBins + 1) * sizeof(long long)), "cudaMallocHost")) !=
       COLA_OK)
     return fail(st);

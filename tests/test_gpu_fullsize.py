@@ -63,9 +63,10 @@ def fixed_cells(s, ids):
     return g >> 20, ((g >> 6) & 16383).double() / 16384.0
 
 
-# default (wide tiles); narrow tiles with: 8-element pipelined passes; + pipelined gather; + 8-element Green;
-# + 8-element C2R; + pipelined C2R; 8-element R2C; plain strided passes, narrow and wide; in-place pipelined passes
-SCHEDULES = [None, 15, 31, 47, 79, 143, 1031, 3, 2051, 6151]
+# default (wide tiles, in-place pipelined passes); narrow tiles with: 8-element pipelined passes; + pipelined
+# gather; + 8-element Green; + 8-element C2R; + pipelined C2R; 8-element R2C; plain strided passes, narrow and wide;
+# in-place pipelined passes; three-buffer pipelined passes with the wide Green pass
+SCHEDULES = [None, 15, 31, 47, 79, 143, 1031, 3, 2051, 6151, 2055]
 
 
 @pytest.mark.parametrize("sched", SCHEDULES)
