@@ -338,13 +338,12 @@ extern "C" int cola_create(const cola_params* params, void* stream, cola_ctx** o
     c->binned = true;
     c->tile_gather = tile_gather_pays(c->bg, c->pg.npart);
   }
-  // meshes of 769 to 1536 cells: the in-place pipelined strided passes hold tiles of 8 pencils
-  // (64-byte row segments) where the three-buffer ones hold 4 (at 1536: 185.6 against 203.2 ms per
-  // PM force evaluation on 1024^3 particles)
-  {
-    const int n = params->nmesh;
-    c->mplan.pipe_inplace = n > 768 && n * 8 <= 12288;
-  }
+  // meshes (and 2LPT lattices) of 769 to 1536 cells: the in-place pipelined strided passes hold
+  // tiles of 8 pencils (64-byte row segments) where the three-buffer ones hold 4 (at 1536: 185.6
+  // against 203.2 ms per PM force evaluation on 1024^3 particles)
+  auto inplace_pays = [](int n) { return n > 768 && n * 8 <= 12288; };
+  c->mplan.pipe_inplace = inplace_pays(params->nmesh);
+  c->lplan.pipe_inplace = inplace_pays(params->np);
   if ((st = cuda_status(cudaMallocHost(&c->edges_host, (kPkMaxBins + 1) * sizeof(long long)), "cudaMallocHost")) !=
       COLA_OK)
     return fail(st);
