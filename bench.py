@@ -318,7 +318,7 @@ def measure_batched(args, torch, device):
     batch = Batch(params, wns, nbins=64, nstreams=args.lanes, stream=stream)
     batch.run(use_graph=False)
     batch.sync()
-    batch.tune(reps=2)
+    batch.tune(reps=5)          # force evaluations of 1-3 ms: more repetitions than the large workload's 2
     batch.run(use_graph=True)   # warm-up + capture + launch
     batch.sync()
     graph_ms = timed(lambda: batch.run(use_graph=True), k)
