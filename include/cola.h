@@ -91,6 +91,13 @@ const char* cola_strerror(int status);
  * Returns COLA_ERR_INVALID for a bad index or nout < 12. */
 int cola_step_scalars(const cola_params* params, int i, double* out, int nout);
 
+/* Linear matter power spectrum at a = 1 of the parameters' cosmology (§1 cosmology; P(k) = A k^n_s
+ * T_BBKS(k)^2 with Gamma = omega_m h, A from sigma8), host only, no context needed.  k: nk
+ * wavenumbers >= 0 in h/Mpc; power (may be NULL) receives P(k) in (Mpc/h)^3, transfer (may be
+ * NULL) T_BBKS(k).  The white-noise amplitudes of cola_ic_2lpt are sqrt(P(k)/V_cell) of these values.
+ * Returns COLA_ERR_INVALID for invalid parameters or a negative or non-finite k. */
+int cola_linear_power(const cola_params* params, const double* k, int nk, double* power, double* transfer);
+
 /* S0 — 2LPT initial conditions (§2.1 growing mode; §2.3 2LPTic-style Gaussian modes).
  * white_noise: device float32 [n], unit Gaussian, one value per lattice site (input).
  * Writes psi1, psi2, s = D1(a_1) Psi1 + D2(a_1) Psi2 and v = 0 (eq. initial_time). */

@@ -188,26 +188,39 @@ def tophat_window(x):
     return np.where(small, 1.0 - x * x / 10.0, w)
 
 
-def _sigma2_integrand_lnk(lnk: float, amp: float, p: Params, radius: float) -> float:
-    k = math.exp(lnk)
-    pk = amp * k ** p.n_s * float(t_bbks(k, p.omega_m, p.h)) ** 2
-    return k ** 3 * pk * float(tophat_window(k * radius)) ** 2 / (2.0 * math.pi ** 2)
+def _bbks_shape(p: Params):
+    """k -> k^ns T_BBKS(k)^2, the shape of the linear spectrum before its amplitude."""
+    return lambda k: k ** p.n_s * t_bbks(k, p.omega_m, p.h) ** 2
 
 
-def sigma2_quad(amp: float, p: Params, radius: float = 8.0) -> float:
-    """sigma^2(R) = (1/2pi^2) int k^2 P(k) W(kR)^2 dk, adaptive quadrature in ln k."""
-    val, _ = integrate.quad(_sigma2_integrand_lnk, math.log(1e-7), math.log(1e3),
-                            args=(amp, p, radius), epsabs=0.0, epsrel=1e-12, limit=2000)
+def sigma2_of(power, radius: float = 8.0) -> float:
+    """sigma^2(R) = (1/2pi^2) int k^2 P(k) W(kR)^2 dk for a spectrum P(k) (k in h/Mpc), by adaptive
+    quadrature in ln k over [1e-7, 1e3] h/Mpc."""
+    def integrand(lnk: float) -> float:
+        k = math.exp(lnk)
+        return k ** 3 * float(power(k)) * float(tophat_window(k * radius)) ** 2 / (2.0 * math.pi ** 2)
+    val, _ = integrate.quad(integrand, math.log(1e-7), math.log(1e3), epsabs=0.0, epsrel=1e-12, limit=2000)
     return val
 
 
-def sigma2_simpson(amp: float, p: Params, radius: float = 8.0, npts: int = 400001) -> float:
-    """Same integral by composite Simpson on a uniform ln k grid (an independent quadrature)."""
+def sigma2_of_simpson(power, radius: float = 8.0, npts: int = 400001) -> float:
+    """The same integral by composite Simpson on a uniform ln k grid (an independent quadrature)."""
     lnk = np.linspace(math.log(1e-7), math.log(1e3), npts)
     k = np.exp(lnk)
-    f = k ** 3 * amp * k ** p.n_s * t_bbks(k, p.omega_m, p.h) ** 2 \
-        * tophat_window(k * radius) ** 2 / (2.0 * math.pi ** 2)
+    f = k ** 3 * power(k) * tophat_window(k * radius) ** 2 / (2.0 * math.pi ** 2)
     return float(integrate.simpson(f, x=lnk))
+
+
+def sigma2_quad(amp: float, p: Params, radius: float = 8.0) -> float:
+    """sigma^2(R) of P(k) = amp k^ns T_BBKS(k)^2 (adaptive quadrature)."""
+    shape = _bbks_shape(p)
+    return sigma2_of(lambda k: amp * shape(k), radius)
+
+
+def sigma2_simpson(amp: float, p: Params, radius: float = 8.0, npts: int = 400001) -> float:
+    """sigma^2(R) of P(k) = amp k^ns T_BBKS(k)^2 (composite Simpson)."""
+    shape = _bbks_shape(p)
+    return sigma2_of_simpson(lambda k: amp * shape(k), radius, npts)
 
 
 def power_amplitude(p: Params) -> float:

@@ -66,6 +66,7 @@ SIGNATURES = {
     "cola_sync": ([_VP], _I),
     "cola_strerror": ([_I], ctypes.c_char_p),
     "cola_step_scalars": ([ctypes.POINTER(CParams), _I, ctypes.POINTER(_D), _I], _I),
+    "cola_linear_power": ([ctypes.POINTER(CParams), ctypes.POINTER(_D), _I, ctypes.POINTER(_D), ctypes.POINTER(_D)], _I),
     "cola_ic_2lpt": ([_VP, _VP, _VP, _VP, _VP, _VP], _I),
     "cola_deposit": ([_VP, _VP, _VP], _I),
     "cola_density_spectrum": ([_VP, _VP, _VP], _I),
@@ -145,6 +146,18 @@ def step_scalars(p: Params, i: int) -> list[float]:
     cp = p.to_c()
     _check(lib.cola_step_scalars(ctypes.byref(cp), i, out, 12), "cola_step_scalars")
     return list(out)
+
+
+def linear_power(p: Params, k) -> tuple[list[float], list[float]]:
+    """The library's linear P(k) and T_BBKS(k) at a = 1 for wavenumbers k (h/Mpc), see cola_linear_power."""
+    lib = load_library()
+    k = [float(x) for x in k]
+    kk = (ctypes.c_double * max(len(k), 1))(*k)
+    pw = (ctypes.c_double * max(len(k), 1))()
+    tr = (ctypes.c_double * max(len(k), 1))()
+    cp = p.to_c()
+    _check(lib.cola_linear_power(ctypes.byref(cp), kk, len(k), pw, tr), "cola_linear_power")
+    return list(pw)[:len(k)], list(tr)[:len(k)]
 
 
 def power_spectrum_noalloc(p: Params, s, nbins: int = 64, stream=None):

@@ -213,6 +213,18 @@ extern "C" int cola_step_scalars(const cola_params* params, int i, double* out, 
   return COLA_OK;
 }
 
+extern "C" int cola_linear_power(const cola_params* params, const double* k, int nk, double* power,
+                                 double* transfer) {
+  if (validate(params) != COLA_OK || nk < 0 || (nk > 0 && !k)) return COLA_ERR_INVALID;
+  const Cosmo cosmo(params->omega_m, params->h, params->n_s, params->sigma8);
+  for (int i = 0; i < nk; ++i) {
+    if (!(k[i] >= 0.0) || !std::isfinite(k[i])) return COLA_ERR_INVALID;
+    if (power) power[i] = cosmo.power(k[i]);
+    if (transfer) transfer[i] = cosmo.transfer(k[i]);
+  }
+  return COLA_OK;
+}
+
 extern "C" void cola_destroy(cola_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);

@@ -4,6 +4,7 @@ cola-drift; §2.1 growth factors) agree with the oracle's independent ones, and 
 rejected on the host before anything touches a device."""
 
 import ctypes
+import math
 import os
 import re
 
@@ -110,3 +111,35 @@ def test_step_scalars_rejects_bad_index(lib):
     out = (ctypes.c_double * 12)()
     assert lib.cola_step_scalars(ctypes.byref(cp), 11, out, 12) == 1
     assert lib.cola_step_scalars(ctypes.byref(cp), 1, out, 11) == 1
+
+
+@pytest.mark.parametrize("kw", [dict(), dict(omega_m=0.3, h=0.67, n_s=1.0, sigma8=0.9)])
+def test_library_linear_power_matches_golden_bbks_and_oracle_amplitude(lib, kw):
+    """The library's own P(k) (host_cosmo.cpp, written independently of the oracle): its transfer
+    function equals the published BBKS coefficients (tests/golden/bbks_transfer.txt) and its
+    amplitude the oracle's sigma8 normalisation, whose integral is pinned by closed forms."""
+    from paper_1507_05329_gb300 import Params, binding
+    from tests.test_oracle_cosmology import bbks_from_golden
+    import numpy as np
+    p = Params(**kw)
+    op = C.Params(**kw)
+    k = np.logspace(-4, 1.5, 47)
+    pw, tr = binding.linear_power(p, k)
+    q = k / (op.omega_m * op.h)
+    np.testing.assert_allclose(tr, bbks_from_golden(q), rtol=1e-13)
+    np.testing.assert_allclose(pw, C.linear_power(k, op), rtol=1e-9)
+    # sigma(8 Mpc/h) of the library's amplitude times the pinned shape, by the oracle's quadrature
+    amp = pw[20] / (k[20] ** op.n_s * tr[20] ** 2)
+    assert math.sqrt(C.sigma2_quad(amp, op)) == pytest.approx(op.sigma8, rel=1e-8)
+
+
+def test_linear_power_rejects_bad_input(lib):
+    from paper_1507_05329_gb300 import Params
+    import numpy as np
+    cp = Params().to_c()
+    k = (ctypes.c_double * 2)(0.1, -1.0)
+    out = (ctypes.c_double * 2)()
+    assert lib.cola_linear_power(ctypes.byref(cp), k, 2, out, None) == 1
+    assert lib.cola_linear_power(ctypes.byref(cp), k, 1, out, None) == 0
+    bad = Params(np_side=7).to_c()
+    assert lib.cola_linear_power(ctypes.byref(bad), k, 1, out, None) == 1

@@ -129,3 +129,95 @@ def test_constant_drift_ansatz():
     a = C.drift_factor(0.3, 0.4, 0.35, om, -2.5, ansatz=1)
     b = C.drift_factor(0.3, 0.4, 0.35, om, 0.0, ansatz=0)
     assert a == pytest.approx(b, rel=1e-13)
+
+
+# ---- outside pins of the linear spectrum: the BBKS coefficients and the sigma^2 integral ----------
+
+GOLDEN = __import__("os").path.join(__import__("os").path.dirname(__file__), "golden")
+
+
+def bbks_golden():
+    """The five published BBKS coefficients (tests/golden/bbks_transfer.txt, with its citation)."""
+    c = {}
+    for line in open(__import__("os").path.join(GOLDEN, "bbks_transfer.txt")):
+        if line.strip() and not line.startswith("#"):
+            name, value = line.split()
+            c[name] = float(value)
+    return c
+
+
+def bbks_from_golden(q):
+    """T(q) evaluated term by term from the golden coefficients (log-sum form, not the oracle's)."""
+    c = bbks_golden()
+    q = np.asarray(q, dtype=np.float64)
+    poly = 1.0 + c["c1"] * q + (c["c2"] * q) ** 2 + (c["c3"] * q) ** 3 + (c["c4"] * q) ** 4
+    return np.exp(np.log(np.log1p(c["c0"] * q)) - np.log(c["c0"] * q) - 0.25 * np.log(poly))
+
+
+@pytest.mark.parametrize("om,h", [(0.27, 0.7), (0.3, 0.67), (1.0, 0.5)])
+def test_bbks_matches_the_published_coefficients(om, h):
+    # interior q, where every coefficient matters: a one-digit change of any of them moves T by
+    # more than 5e-5 somewhere on this grid
+    q = np.logspace(-3, 2, 61)
+    k = q * om * h
+    np.testing.assert_allclose(C.t_bbks(k, om, h), bbks_from_golden(q), rtol=1e-13)
+
+
+def test_bbks_typos_are_visible_to_the_pin():
+    """Each coefficient, changed in its last printed digit, moves T by > 5e-5 somewhere in q (far
+    above the pin's 1e-13)."""
+    c = bbks_golden()
+    q = np.logspace(-3, 2, 61)
+
+    def t(cc):
+        poly = 1.0 + cc["c1"] * q + (cc["c2"] * q) ** 2 + (cc["c3"] * q) ** 3 + (cc["c4"] * q) ** 4
+        return np.log1p(cc["c0"] * q) / (cc["c0"] * q) * poly ** -0.25
+
+    base = t(c)
+    for name, step in (("c0", 0.01), ("c1", 0.01), ("c2", 0.1), ("c3", 0.01), ("c4", 0.01)):
+        cc = dict(c)
+        cc[name] += step
+        assert np.max(np.abs(t(cc) / base - 1.0)) > 5e-5, name
+
+
+def test_bbks_shape_agrees_with_eisenstein_hu_zero_baryon():
+    """An independent fit to the same CDM physics: Eisenstein & Hu 1998 (ApJ 496, 605) eqs. (28)-(29)
+    without baryons, T0 = L0 / (L0 + C0 q^2), L0 = ln(2e + 1.8 q), C0 = 14.2 + 731 / (1 + 62.5 q),
+    with q = k / (Gamma h Mpc^-1) at Theta_2.7 = 1.  The two fits agree to 4% from q = 1e-3 to 30;
+    a wrong power, a swapped coefficient or a dropped term breaks that."""
+    om, h = 0.27, 0.7
+    q = np.logspace(-3, 1.5, 91)
+    l0 = np.log(2.0 * math.e + 1.8 * q)
+    c0 = 14.2 + 731.0 / (1.0 + 62.5 * q)
+    t_eh = l0 / (l0 + c0 * q * q)
+    ratio = C.t_bbks(q * om * h, om, h) / t_eh
+    assert np.max(np.abs(ratio - 1.0)) < 0.045
+
+
+def _power_law(amp, n):
+    return lambda k: amp * np.asarray(k, dtype=np.float64) ** n
+
+
+@pytest.mark.parametrize("radius", [5.0, 8.0])
+def test_sigma2_of_power_laws_matches_real_space_closed_forms(radius):
+    """sigma^2(R) of P = A k^n with a top hat, from real space: sigma^2 = <xi(|x - y|)> over pairs of
+    points of the ball.  For n = -2, xi = A / (4 pi r); for n = -1, xi = A / (2 pi^2 r^2).  Two
+    uniform points in a ball of radius R have <1/r> = 6 / (5R) and <1/r^2> = 9 / (4 R^2) (from their
+    distance density 3 r^2/R^3 (1 - 3r/(4R) + r^3/(16 R^3)) on [0, 2R]), so sigma^2 = 3A / (10 pi R)
+    and 9A / (8 pi^2 R^2).  This pins the 1/(2 pi^2) factor, the k^2 dk measure and the window."""
+    amp = 3.7
+    cases = ((-2.0, 3.0 * amp / (10.0 * math.pi * radius), 2e-6),   # the low-k cut leaves ~5e-7
+             (-1.0, 9.0 * amp / (8.0 * math.pi ** 2 * radius ** 2), 1e-7))
+    for n, closed, tol in cases:
+        assert C.sigma2_of(_power_law(amp, n), radius) == pytest.approx(closed, rel=tol)
+        assert C.sigma2_of_simpson(_power_law(amp, n), radius) == pytest.approx(closed, rel=tol)
+
+
+def test_sigma2_of_white_noise_is_the_inverse_volume():
+    """P = A (white noise): the mean over a ball of volume V has variance A / V (Parseval), less the
+    part of the integral beyond the upper limit k = 1e3 h/Mpc, 9 A / (4 pi^2 R^3 X) with X = 1e3 R
+    (the window's tail 9 cos^2 x / x^4 averaged)."""
+    amp, radius = 2.0, 8.0
+    x_max = 1e3 * radius
+    expected = 3.0 * amp / (4.0 * math.pi * radius ** 3) - 9.0 * amp / (4.0 * math.pi ** 2 * radius ** 3 * x_max)
+    assert C.sigma2_of(_power_law(amp, 0.0), radius) == pytest.approx(expected, rel=2e-6)
