@@ -24,8 +24,10 @@
  *   - Errors: every int-returning call returns a cola_status.  Argument errors are found on the
  *     host before anything is launched.  Device-side conditions (fixed-point overflow,
  *     non-finite particle state) set a sticky flag that cola_sync() reports.
- *   - One context per device and stream; a context is not thread safe.  The library keeps no
- *     global state besides the contexts.
+ *   - One context per device and stream; a context is not thread safe.  Besides the contexts the
+ *     library keeps only process-wide records of which kernels already had their shared-memory
+ *     limit raised on which device, and the static scratch array of the allocation-free entry
+ *     point (cola_power_spectrum_noalloc, at the end of this header).
  */
 #ifndef COLA_H
 #define COLA_H
@@ -368,9 +370,11 @@ int cola_profile_read(cola_ctx* ctx, double* ms, long long* launches, int nstage
  *   s      : device float32 [3][np^3] displacements (mesh cells), 16-byte aligned.
  *   pk     : device double [3][nbins], as for cola_power_spectrum; 1 <= nbins <= 128.
  *   stream : cudaStream_t to enqueue on (NULL = legacy default stream).
- * Asynchronous: results are ready when the stream reaches them.  The first call on each device
- * resolves the array's device address (cudaGetSymbolAddress) and raises the FFT kernels' shared
- * memory limit; make that first call before any stream capture.  Every call shares the array:
+ * Asynchronous: results are ready when the stream reaches them.  The call runs on the current
+ * device, whose copy of the array it uses: s, pk and the stream must belong to that device.  The
+ * first call on each device resolves the array's device address (cudaGetSymbolAddress), and each
+ * kernel's first launch on a device raises its shared-memory limit (host-side attribute calls, no
+ * allocation); make that first call before any stream capture.  Every call shares the array:
  * calls that overlap on the GPU (other streams or threads) race and give wrong results. */
 #define COLA_NOALLOC_MAX_MESH 64
 #define COLA_NOALLOC_MAX_NP 128

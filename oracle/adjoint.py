@@ -7,7 +7,7 @@ eqs. cola-kick and cola-drift, PM force of §2.2/§2.3, 2LPT of §2.1/§2.3) wit
 differentiation needs: the CIC weights are the continuous ones (``cic_exact_mesh`` and exact
 interpolation weights), since the fixed-point weights are piecewise constant in position (their
 derivative is zero almost everywhere).  The derivative of a CIC weight is taken one-sided at cell
-faces, from the cell floor(x) chooses (reading 17).
+faces, from the cell floor(x) chooses (a reading: the paper has no adjoint).
 
 Loss (the differentiable workload): L = sum_g (delta_g - delta_target_g)^2 over a CIC density
 contrast on an ngrid^3 grid of the final positions.

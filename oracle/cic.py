@@ -5,7 +5,7 @@ Test infrastructure only (see ``oracle/__init__.py``).
 Paper passages: the PM force assigns particles to a uniform mesh and interpolates the force
 back (§2.3, the (3 x 1296)^3 PM mesh; Appendix A, the PM force resolution) and the power
 spectrum assigns densities with CIC (§3.3).  The paper does not define the arithmetic of the
-assignment; this build fixes it as a deterministic fixed-point scheme ("readings"):
+assignment; this oracle fixes it as a deterministic fixed-point scheme (a reading, not the paper's):
 
   * a particle with lattice index q (per axis, 0..Np-1) and displacement s (PM cells) sits at
     mesh coordinate q*r + s, r = N/Np;

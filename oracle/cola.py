@@ -12,8 +12,9 @@ Paper passages:
 
 State: s = x - q (total displacement, PM cells), v_res (canonical, PM cells per unit time,
 H0 = 1).  The 2LPT acceleration is F_2LPT = (3/2)(Om/a)[D1 Psi1 + (D2 - D1^2) Psi2]
-(reading 4).  The final kick ends at a_{n_step} and the last step does not drift
-(reading 3).
+(a reading: the paper names x_2LPT's acceleration without writing it; this follows from the 2LPT
+growth equations).  The final kick ends at a_{n_step} and the last step does not drift (§2.2,
+eq. drift-a: positions at a_i = i/n_step, velocities at the half steps).
 """
 
 from __future__ import annotations
@@ -57,7 +58,8 @@ def snapshot(i: int, s, v, psi1, psi2, p: cosmology.Params, a_snap: float, force
     (§2.2: the kick/drift equations also interpolate between steps), from the state (s_i, v_res at
     a_{i-1/2}) before step i: kick as in ``step``, then the drift of eq. (cola-drift) and the 2LPT
     growth taken only up to a_snap.  The residual velocity between kicks is v_res(a_{i+1/2})
-    (reading 18).  a_i <= a_snap <= a_{i+1} (a_snap = a_i = 1 after the last step)."""
+    (a reading: the paper's remark that an acceleration term could improve this is not applied).
+    a_i <= a_snap <= a_{i+1} (a_snap = a_i = 1 after the last step)."""
     c = cosmology.step_scalars(p, i)
     a_i = c["a"]
     if not (a_i - 1e-12 <= a_snap <= c["a_next"] + 1e-12):
@@ -79,7 +81,7 @@ def snapshot(i: int, s, v, psi1, psi2, p: cosmology.Params, a_snap: float, force
 
 
 def final_velocity(v_res, psi1, psi2, p: cosmology.Params, a: float = 1.0):
-    """Canonical velocity v = v_res + a^2 dx_2LPT/dt at a (reading 15)."""
+    """Canonical velocity v = v_res + a^2 dx_2LPT/dt at a (H0 = 1, lengths in PM cells; the paper's output velocities, §2.2 eq. motion)."""
     f1, f2 = cosmology.lpt_velocity_factors(a, p.omega_m)
     return v_res + f1 * psi1 + f2 * psi2
 

@@ -10,7 +10,7 @@ Paper passages followed:
   * drift factor ............................... §2.2 eq. (cola-drift) with the ansatz eq. (ansatz-drift)
   * kick factor ................................ §2.2 eq. (cola-kick) with the ansatz eq. (ansatz-kick)
   * constant-velocity drift ansatz (TZE) ....... §2.1 (the alternative ansatz v_res = const)
-Readings where the paper is silent or garbled (listed in the design doc):
+Readings where the paper is silent or garbled:
   * Omega(a) = Om / (Om + OL a^3): the printed formula lost its division.
   * the 2LPT acceleration uses the growth ODEs d/dt(a^2 dD1/dt) = 3/2 Om D1 / a and
     d/dt(a^2 dD2/dt) = 3/2 Om (D2 - D1^2) / a, which the paper does not write out.

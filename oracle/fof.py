@@ -7,7 +7,7 @@ and §3.2 (haloes identified with linking length 0.2 times the mean particle sep
 2LPT).  Two particles are friends when their periodic distance is at most the linking length;
 a group is a connected component of the friendship graph (friends of friends).
 
-Readings (reading 20): the distance is measured exactly on the fixed-point coordinates
+Readings where the paper is silent: the distance is measured exactly on the fixed-point coordinates
 G of the deposit (20 fractional bits per mesh cell), with the linking length
 l = rint(b * (N / N_p) * 2^20) in the same units and the test d^2 <= l^2 in integers, so no
 rounding decides a link.  A group is labelled by its smallest particle id.  A halo is a group of at

@@ -35,7 +35,8 @@ def odd_mode(m: np.ndarray, n: int) -> np.ndarray:
     """m with the Nyquist mode (|m| = n/2) set to 0.
 
     A single factor i k_j is odd under k -> -k; on the Nyquist plane -k aliases to k, so the
-    factor is set to 0 there to keep the inverse transform real (reading 6).
+    factor is set to 0 there to keep the inverse transform real (a reading: the paper does not
+    state its gradient's Nyquist treatment).
     """
     return np.where(np.abs(m) * 2 == n, 0, m)
 

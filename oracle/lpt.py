@@ -4,7 +4,7 @@ Test infrastructure only (see ``oracle/__init__.py``).
 
 Paper passages: the 2LPT growing mode x = q + D1 Psi1 + D2 Psi2 (§2.1) generated by a 2LPTic
 style code from Gaussian random modes (§2.3).  The paper does not write the 2LPT field equations;
-the textbook ones are used (reading 5):
+the textbook ones are used (a reading; signs fixed by D2 < 0):
 
     Psi1 = -grad phi1,  nabla^2 phi1 = delta_L;           Psi1(k) =  i k delta_L / k^2
     phi1_ij(k) = k_i k_j delta_L / k^2

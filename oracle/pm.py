@@ -11,7 +11,7 @@ of mode m is k = 2 pi m / N, so
 with the continuous Green function -1/k^2 and the gradient kernel of the 4-point central
 difference, D(k) = (8 sin k - sin 2k) / 6 (k in radians per cell), which is 0 on the Nyquist
 plane.  No deconvolution of the CIC window.  The paper names only "the PM force"; this reading
-(reading 6) is the one whose pair force matches Newton beyond ~3 cells with per-cent
+(not stated in the paper) is the one whose pair force matches Newton beyond ~3 cells with per-cent
 scatter (Appendix A), which the continuous i k kernel does not (its point-source force rings at
 the mesh scale).
 """

@@ -8,9 +8,10 @@ mode is counted twice, P(k) = V^-1 <|delta(k)|^2> per bin, plotted against the m
 bin's modes.  The paper corrects the CIC smoothing and aliasing with the procedure of Jing
 (2005); ``power_spectrum(..., cic_correct=True, n_particles=n)`` applies that correction for a
 locally flat spectrum: per mode P = P_raw / C2(k) - V/n, with the alias-summed CIC window
-C2(k) = sum_n W^2(k + 2 k_N n) = prod_i (1 - (2/3) sin^2(pi m_i / N)) (reading 19).
+C2(k) = sum_n W^2(k + 2 k_N n) = prod_i (1 - (2/3) sin^2(pi m_i / N)) (the flat-spectrum form of
+Jing's correction; his iteration on a local power-law slope is not applied).
 
-Readings: delta(k) = (V/N^3) sum_x delta_x e^{-i k.x}, so P = V |DFT|^2 / N^6.  Bins
+Readings where the paper is silent: delta(k) = (V/N^3) sum_x delta_x e^{-i k.x}, so P = V |DFT|^2 / N^6.  Bins
 are log spaced between the fundamental k_f = 2 pi / L and the Nyquist k_N = pi N / L (the paper
 uses linear bins of 0.01 h/Mpc; the 64 log bins are the workload's).  A mode's bin is decided on
 its integer |m|^2 against integer edges T_b = ceil(e_b^2 - 1e-9), e_b = (N/2)^(b/nbins), so no

@@ -165,12 +165,16 @@ def power_spectrum_noalloc(p: Params, s, nbins: int = 64, stream=None):
     64^3).  Returns a new [3, nbins] float64 tensor; the library itself allocates nothing."""
     import torch
     lib = load_library()
-    st = stream if stream is not None else torch.cuda.current_stream()
-    pk = torch.empty((3, nbins), dtype=torch.float64, device=s.device)
-    cp = p.to_c()
-    _check(lib.cola_power_spectrum_noalloc(ctypes.byref(cp), _ptr(s, torch, (3, p.n), torch.float32),
-                                           _ptr(pk, torch), int(nbins), ctypes.c_void_p(st.cuda_stream)),
-           "cola_power_spectrum_noalloc")
+    if not s.is_cuda:
+        raise ValueError("COLA tensors must live on a CUDA device")
+    # the library resolves its static scratch on the current device: make that s's device
+    with torch.cuda.device(s.device):
+        st = stream if stream is not None else torch.cuda.current_stream(s.device)
+        pk = torch.empty((3, nbins), dtype=torch.float64, device=s.device)
+        cp = p.to_c()
+        _check(lib.cola_power_spectrum_noalloc(ctypes.byref(cp), _ptr(s, torch, (3, p.n), torch.float32),
+                                               _ptr(pk, torch), int(nbins), ctypes.c_void_p(st.cuda_stream)),
+               "cola_power_spectrum_noalloc")
     return pk
 
 

@@ -17,9 +17,6 @@
 namespace cola {
 namespace {
 
-constexpr int kFracBits = 20;
-constexpr long long kFracOne = 1LL << kFracBits;
-constexpr int kWeightOne = 1 << 14;
 
 int check_launch(const char* what) {
   const cudaError_t e = cudaGetLastError();
@@ -35,17 +32,6 @@ unsigned grid_for(long long work, int threads) {
   const long long cap = 152LL * 16 * 4;
   if (b > cap) b = cap;
   return (unsigned)(b < 1 ? 1 : b);
-}
-
-__device__ __forceinline__ long long fixed_coord(int q, float s, long long r_fixed, long long modulus) {
-  long long g = (long long)q * r_fixed + __float2ll_rn(s * (float)kFracOne);
-  if (g < 0) g += modulus;
-  else if (g >= modulus) g -= modulus;
-  if ((unsigned long long)g >= (unsigned long long)modulus) {
-    g %= modulus;
-    if (g < 0) g += modulus;
-  }
-  return g;
 }
 
 __device__ __forceinline__ void lattice_of(long long id, int np, int* q) {

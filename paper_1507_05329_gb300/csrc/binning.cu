@@ -26,9 +26,6 @@
 namespace cola {
 namespace {
 
-constexpr int kFracBits = 20;
-constexpr long long kFracOne = 1LL << kFracBits;
-constexpr int kWeightOne = 1 << 14;
 constexpr int kThreads = 256;
 
 int check_launch(const char* what) {
@@ -38,17 +35,6 @@ int check_launch(const char* what) {
     return COLA_ERR_CUDA;
   }
   return COLA_OK;
-}
-
-__device__ __forceinline__ long long fixed_coord(int q, float s, long long r_fixed, long long modulus) {
-  long long g = (long long)q * r_fixed + __float2ll_rn(s * (float)kFracOne);
-  if (g < 0) g += modulus;
-  else if (g >= modulus) g -= modulus;
-  if ((unsigned long long)g >= (unsigned long long)modulus) {
-    g %= modulus;
-    if (g < 0) g += modulus;
-  }
-  return g;
 }
 
 // Bin entries hold the lattice coordinates packed as qx << 20 | qy << 10 | qz (np <= 1024).
@@ -593,14 +579,12 @@ int launch_excl_scan(const unsigned* cnt, int m, unsigned* seg, unsigned* off, u
 }
 
 int launch_binning(const ParticleGeom& pg, const BinGeom& b, const float* s, BinBuffers& bb, cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
+  if (first_use_on_device(reinterpret_cast<const void*>(&launch_binning))) {
     cudaFuncSetAttribute(k_deposit_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
     cudaFuncSetAttribute(k_gather_tiles<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
     cudaFuncSetAttribute(k_gather_tiles<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
     cudaFuncSetAttribute(k_gather_tiles_pipe<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024);
     cudaFuncSetAttribute(k_gather_tiles_pipe<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024);
-    attr = true;
   }
   const long long rows = (long long)pg.np * pg.np;
   const unsigned grid = (unsigned)(rows < 152LL * 64 ? rows : 152LL * 64);

@@ -76,6 +76,10 @@ void fft_plan_steps(FftPlan* plan);        // fills nbp / nsp from dev.n and dev
 void fft_plan_free(FftPlan* plan);
 void fft_set_smem_limits();                // raise the dynamic shared-memory limit of the FFT kernels
 
+// True the first time it is called for `key` on the current device (thread safe).  Kernel attributes
+// (the dynamic shared-memory limit) are per device, so every setter is keyed by (device, kernel).
+bool first_use_on_device(const void* key);
+
 // Geometry of a 3D field of side n in the in-place real-to-complex layout:
 // complex rows of pc = (n/2+1 rounded up to even) entries, real rows of 2*pc floats.
 struct Grid3 {
@@ -120,6 +124,30 @@ int launch_deposit(const ParticleGeom& pg, const float* s, unsigned long long* r
 // summing rho here when sum_mesh) differs from n 2^42, i.e. if some cell wrapped; resets acc.
 int launch_mass_check(const ParticleGeom& pg, const unsigned long long* rho, bool sum_mesh, unsigned long long* acc,
                       int* flags, cudaStream_t st);
+
+// Fixed-point particle coordinates shared by the deposit, the gathers, the adjoint and FoF: a
+// particle at lattice index q (per axis) and displacement s (mesh cells) sits at
+// G = (q R + rint(s 2^20)) mod N 2^20, R = (N/np) 2^20; its cell is G >> 20 and its 14-bit CIC
+// weight fraction (G >> 6) & (2^14 - 1).  Every kernel must take the same integers, which makes the
+// deposit bit-exact and the interpolation use the deposit's own weights.
+constexpr int kFracBits = 20;
+constexpr long long kFracOne = 1LL << kFracBits;
+constexpr int kWeightOne = 1 << 14;
+
+#ifdef __CUDACC__
+// G of one axis.  A NaN or huge s wraps into [0, modulus) (the final % catches what one
+// conditional add cannot), so no kernel can index outside the mesh.
+__device__ __forceinline__ long long fixed_coord(int q, float s, long long r_fixed, long long modulus) {
+  long long g = (long long)q * r_fixed + __float2ll_rn(s * (float)kFracOne);
+  if (g < 0) g += modulus;
+  else if (g >= modulus) g -= modulus;
+  if ((unsigned long long)g >= (unsigned long long)modulus) {
+    g %= modulus;
+    if (g < 0) g += modulus;
+  }
+  return g;
+}
+#endif
 
 #ifdef __CUDACC__
 // Adds a thread's 128-bit partial (lo, hi) to the global accumulator acc[0..1] (exact, any order).

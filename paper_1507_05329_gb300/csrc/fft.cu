@@ -2,6 +2,10 @@
 // among the pipelined, fast and generic kernels of each pass.
 #include "fft_core.cuh"
 
+#include <mutex>
+#include <set>
+#include <utility>
+
 namespace cola {
 using namespace fftk;
 namespace {
@@ -217,12 +221,17 @@ int fft_plan_init(FftPlan* plan, int n) {
   if (cudaMemcpy(plan->tw, h.data(), n * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess)
     return COLA_ERR_CUDA;
   plan->dev.tw = plan->tw;
-  static bool attrs_set = false;
-  if (!attrs_set) {
-    generic_set_smem_limits();
-    attrs_set = true;
-  }
+  if (first_use_on_device(reinterpret_cast<const void*>(&generic_set_smem_limits))) generic_set_smem_limits();
   return COLA_OK;
+}
+
+bool first_use_on_device(const void* key) {
+  static std::mutex mu;
+  static std::set<std::pair<int, const void*>> done;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) dev = -1;
+  std::lock_guard<std::mutex> lock(mu);
+  return done.insert({dev, key}).second;
 }
 
 void fft_set_smem_limits() { generic_set_smem_limits(); }

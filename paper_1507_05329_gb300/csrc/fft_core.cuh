@@ -918,14 +918,12 @@ struct HalfPairS {
   __device__ __forceinline__ float4 ld2(int k, int w) const { return pack2((*this)(k, w), (*this)(k, w + 1)); }
 };
 
-// Raises a kernel's dynamic shared-memory limit the first time it is launched (host side).
+// Raises a kernel's dynamic shared-memory limit the first time it is launched on the current
+// device (host side; the attribute is per device).
 template <class K>
 inline void ensure_smem(K kernel) {
-  static std::mutex mu;
-  static std::unordered_set<const void*> done;
-  std::lock_guard<std::mutex> lock(mu);
-  const void* key = reinterpret_cast<const void*>(kernel);
-  if (done.insert(key).second) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  if (first_use_on_device(reinterpret_cast<const void*>(kernel)))
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
 }
 
 }  // namespace fftk

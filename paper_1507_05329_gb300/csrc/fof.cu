@@ -19,7 +19,6 @@
 namespace cola {
 namespace {
 
-constexpr int kFracBits = 20;
 constexpr int kFlagIterations = 4;   // union-find did not converge (never expected; reported)
 
 int check_launch(const char* what) {
@@ -36,17 +35,6 @@ unsigned grid_for(long long work, int threads) {
   const long long cap = 152LL * 16 * 4;
   if (b > cap) b = cap;
   return (unsigned)(b < 1 ? 1 : b);
-}
-
-__device__ __forceinline__ long long fixed_coord(int q, float s, long long r_fixed, long long modulus) {
-  long long g = (long long)q * r_fixed + __float2ll_rn(s * (float)(1LL << kFracBits));
-  if (g < 0) g += modulus;
-  else if (g >= modulus) g -= modulus;
-  if ((unsigned long long)g >= (unsigned long long)modulus) {
-    g %= modulus;
-    if (g < 0) g += modulus;
-  }
-  return g;
 }
 
 // minimum image of a difference in (-modulus, modulus)

@@ -12,9 +12,6 @@
 namespace cola {
 namespace {
 
-constexpr int kFracBits = 20;
-constexpr long long kFracOne = 1LL << kFracBits;
-constexpr int kWeightOne = 1 << 14;
 
 int check_launch(const char* what) {
   const cudaError_t e = cudaGetLastError();
@@ -34,17 +31,6 @@ unsigned grid_for(long long work, int threads) {
 
 // Fixed-point mesh coordinate of one axis: G = (q R + rint(s 2^20)) mod (N 2^20).  Displacements
 // below one box length wrap with one compare; larger ones take the modulo path.
-__device__ __forceinline__ long long fixed_coord(int q, float s, long long r_fixed, long long modulus) {
-  long long g = (long long)q * r_fixed + __float2ll_rn(s * (float)kFracOne);
-  if (g < 0) g += modulus;
-  else if (g >= modulus) g -= modulus;
-  if ((unsigned long long)g >= (unsigned long long)modulus) {
-    g %= modulus;
-    if (g < 0) g += modulus;
-  }
-  return g;
-}
-
 // Particles are processed by lattice rows: blockIdx.x (grid-stride) indexes the row (qx, qy) and
 // the threads walk qz, so the lattice index needs one division per row and none per particle.
 constexpr int kRowThreads = 256;
