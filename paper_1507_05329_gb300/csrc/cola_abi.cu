@@ -63,7 +63,7 @@ Grid3 make_grid(int n) {
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
-constexpr int kPkBlocks = 304;
+constexpr int kPkBlocks = 1216;   // 8 CTAs of 256 threads per SM: enough loads in flight
 constexpr int kPkMaxBins = 128;
 
 // Integer |m|^2 lower edges of nbins log bins between |m| = 1 and |m| = N/2.
@@ -236,7 +236,7 @@ extern "C" void cola_destroy(cola_ctx* c) {
   if (c->edges_host) cudaFreeHost(c->edges_host);
   fft_plan_free(&c->mplan);
   fft_plan_free(&c->lplan);
-  void* bufs[] = {c->arena,    c->dtab,     c->amp_m2,  c->edges, c->pk_partials,
+  void* bufs[] = {c->arena,    c->dtab,     c->amp_m2,  c->edges, c->pk_partials, c->pk_geom,
                   c->flags,    c->mass_acc, c->bin_mem, c->adj_mem,     c->fof_mem,  c->fof_sums};
   for (void* b : bufs)
     if (b) cudaFree(b);
@@ -322,8 +322,9 @@ extern "C" int cola_create(const cola_params* params, void* stream, cola_ctx** o
   }
   c->pk_blocks = kPkBlocks;
   if ((st = cuda_status(cudaMalloc(&c->edges, (kPkMaxBins + 1) * sizeof(long long)), "cudaMalloc")) != COLA_OK ||
-      (st = cuda_status(cudaMalloc(&c->pk_partials, (size_t)kPkBlocks * 3 * kPkMaxBins * sizeof(double)),
+      (st = cuda_status(cudaMalloc(&c->pk_partials, (size_t)kPkBlocks * 2 * kPkMaxBins * sizeof(double)),
                         "cudaMalloc")) != COLA_OK ||
+      (st = cuda_status(cudaMalloc(&c->pk_geom, 2 * kPkMaxBins * sizeof(double)), "cudaMalloc")) != COLA_OK ||
       (st = cuda_status(cudaMalloc(&c->flags, sizeof(int)), "cudaMalloc")) != COLA_OK ||
       (st = cuda_status(cudaMalloc(&c->mass_acc, 2 * sizeof(unsigned long long)), "cudaMalloc")) != COLA_OK)
     return fail(st);
@@ -478,9 +479,15 @@ extern "C" int cola_power_spectrum_ex(cola_ctx* c, const float* s, double* pk, i
   const double pscale = vol / (nn * nn * nn * nn * nn * nn);
   const double kfund = 2.0 * M_PI / c->p.box;
   const int corr = (flags & COLA_PK_CIC_CORRECT) ? 1 : 0;
-  COLA_TRY(STAGED(kStPk, launch_pk_bins(c->mesh, c->cbuf[2], c->edges, nbins, pscale, kfund, corr,
-                                        vol / (double)c->pg.npart, c->pk_partials, c->pk_blocks, c->stream)));
-  return STAGED(kStPk, launch_pk_finish(c->pk_partials, c->pk_blocks, nbins, pk, c->stream));
+  if (c->pk_geom_nbins != nbins) {   // once per bin count: mode counts and mean |k| of the bins
+    COLA_TRY(STAGED(kStPk, launch_pk_geometry(c->mesh, c->edges, nbins, c->pk_partials, c->pk_blocks, c->pk_geom,
+                                              c->stream)));
+    c->pk_geom_nbins = nbins;
+  }
+  COLA_TRY(STAGED(kStPk, launch_pk_bins(c->mesh, c->cbuf[2], c->edges, nbins, corr, c->pk_partials, c->pk_blocks,
+                                        c->stream)));
+  return STAGED(kStPk, launch_pk_finish(c->pk_partials, c->pk_blocks, nbins, c->pk_geom, kfund, pscale,
+                                        corr ? vol / (double)c->pg.npart : 0.0, pk, c->stream));
 }
 
 extern "C" int cola_power_spectrum(cola_ctx* c, const float* s, double* pk, int nbins) {

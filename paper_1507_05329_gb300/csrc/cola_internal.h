@@ -263,10 +263,17 @@ int launch_fof(const ParticleGeom& pg, const FofGeom& f, const float* s, const F
 // ceil(m / 4096) partial sums.
 int launch_excl_scan(const unsigned* cnt, int m, unsigned* seg, unsigned* off, unsigned* cur, cudaStream_t st);
 
-// Power spectrum binning of a forward spectrum (side n).
-int launch_pk_bins(const Grid3& g, const float2* dk, const long long* edges, int nbins, double pscale, double kfund,
-                   int cic_correct, double shot, double* partials, int nblocks, cudaStream_t st);
-int launch_pk_finish(const double* partials, int nblocks, int nbins, double* pk, cudaStream_t st);
+// Power spectrum binning of a forward spectrum (side n).  launch_pk_geometry writes the bins' sum of
+// |m| and mode count (they depend only on n and the edges) to geom[2][nbins]; launch_pk_bins sums the
+// modes' power (over C2 when cic_correct) into partials[nblocks][nbins]; launch_pk_finish combines
+// them into pk[3][nbins] (mean |k| = kfund mean |m|, P = pscale mean power - shot, counts).
+// partials holds 2 nblocks nbins doubles (the geometry pass uses both halves).
+int launch_pk_geometry(const Grid3& g, const long long* edges, int nbins, double* partials, int nblocks,
+                       double* geom, cudaStream_t st);
+int launch_pk_bins(const Grid3& g, const float2* dk, const long long* edges, int nbins, int cic_correct,
+                   double* partials, int nblocks, cudaStream_t st);
+int launch_pk_finish(const double* partials, int nblocks, int nbins, const double* geom, double kfund, double pscale,
+                     double shot, double* pk, cudaStream_t st);
 int launch_dense_spectrum(const Grid3& g, const float2* src, float* dst, cudaStream_t st);
 
 }  // namespace cola
@@ -292,6 +299,8 @@ struct cola_ctx {
   int edges_nbins = 0;
   double* pk_partials = nullptr;
   int pk_blocks = 0;
+  double* pk_geom = nullptr;              // [2][nbins]: sum of |m| and mode count per bin
+  int pk_geom_nbins = 0;                  // bins the geometry was computed for (0: none yet)
   int* flags = nullptr;                   // sticky device error flags
   unsigned long long* mass_acc = nullptr; // 128-bit total of the fixed-point mesh (overflow check)
   bool binned = false;                    // tile-wise deposit (else direct atomics)

@@ -5,7 +5,7 @@
 // heap, or real-time loops that forbid allocator calls and their implicit synchronisation.  For
 // them cola_power_spectrum_noalloc measures P(k) of a small realisation without a context: every
 // scratch buffer it needs (the fixed-point density mesh, the half spectrum, the per-block partial
-// sums, the FFT twiddles and the bin edges) lives in one file-scope device array of fixed size.
+// sums, the bins' geometry, the FFT twiddles and the bin edges) lives in one file-scope device array of fixed size.
 //
 // That array costs COLA_NOALLOC_SCRATCH_BYTES (about 3.4 MB) on every GPU that loads the library,
 // for as long as the process lives.  All calls share it and it keeps the last call's contents:
@@ -27,15 +27,17 @@ constexpr int kBlocks = 64;   // P(k) partial-sum blocks
 constexpr size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
 constexpr size_t kRhoBytes = round256((size_t)kMaxMesh * kMaxMesh * kMaxMesh * sizeof(unsigned long long));
 constexpr size_t kSpecBytes = round256((size_t)kMaxMesh * kMaxMesh * (kMaxMesh / 2 + 2) * sizeof(float2));
-constexpr size_t kPartBytes = round256((size_t)kBlocks * 3 * kMaxBins * sizeof(double));
+constexpr size_t kPartBytes = round256((size_t)kBlocks * 2 * kMaxBins * sizeof(double));
 constexpr size_t kEdgeBytes = round256((kMaxBins + 1) * sizeof(long long));
 constexpr size_t kTwBytes = round256(kMaxMesh * sizeof(float2));
+constexpr size_t kGeomBytes = round256(2 * kMaxBins * sizeof(double));
 constexpr size_t kFlagBytes = 256;
 constexpr size_t kOffSpec = kRhoBytes;
 constexpr size_t kOffPart = kOffSpec + kSpecBytes;
 constexpr size_t kOffEdge = kOffPart + kPartBytes;
 constexpr size_t kOffTw = kOffEdge + kEdgeBytes;
-constexpr size_t kOffFlag = kOffTw + kTwBytes;
+constexpr size_t kOffGeom = kOffTw + kTwBytes;
+constexpr size_t kOffFlag = kOffGeom + kGeomBytes;
 constexpr size_t kTotal = kOffFlag + kFlagBytes;
 static_assert(kTotal <= COLA_NOALLOC_SCRATCH_BYTES, "scratch layout exceeds the documented size");
 
@@ -132,6 +134,7 @@ extern "C" int cola_power_spectrum_noalloc(const cola_params* p, const float* s,
   auto* edg = reinterpret_cast<long long*>(base + kOffEdge);
   auto* tw = reinterpret_cast<float2*>(base + kOffTw);
   auto* flags = reinterpret_cast<int*>(base + kOffFlag);
+  auto* geom = reinterpret_cast<double*>(base + kOffGeom);
 
   const size_t n3 = (size_t)n * n * n;
   if (cudaMemsetAsync(rho, 0, n3 * sizeof(unsigned long long), st) != cudaSuccess) return COLA_ERR_CUDA;
@@ -143,7 +146,8 @@ extern "C" int cola_power_spectrum_noalloc(const cola_params* p, const float* s,
   if (r == COLA_OK) r = launch_pencils(plan, g, 1, -1, spec, st);
   if (r == COLA_OK) r = launch_pencils(plan, g, 0, -1, spec, st);
   const double pscale = std::pow(p->box, 3) / std::pow((double)n, 6);
-  if (r == COLA_OK) r = launch_pk_bins(g, spec, edg, nbins, pscale, 2.0 * M_PI / p->box, 0, 0.0, part, kBlocks, st);
-  if (r == COLA_OK) r = launch_pk_finish(part, kBlocks, nbins, pk, st);
+  if (r == COLA_OK) r = launch_pk_geometry(g, edg, nbins, part, kBlocks, geom, st);
+  if (r == COLA_OK) r = launch_pk_bins(g, spec, edg, nbins, 0, part, kBlocks, st);
+  if (r == COLA_OK) r = launch_pk_finish(part, kBlocks, nbins, geom, 2.0 * M_PI / p->box, pscale, 0.0, pk, st);
   return r;
 }

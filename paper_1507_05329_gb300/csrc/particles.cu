@@ -279,20 +279,39 @@ constexpr int kMaxBins = 128;
 // runs of lanes.  A segmented scan in a fixed shuffle order sums each run, whose last lane adds it
 // to the warp's own histogram; warps and blocks are then summed in index order, so the reduction
 // order is fixed and the result is bit-reproducible.
-// cic_correct: per mode P / C2(m) - shot, C2 = prod_i (1 - (2/3) sin^2(pi m_i / n)) the CIC window
-// squared summed over its aliases (Jing 2005 for a locally flat spectrum), shot = V / particles.
-__global__ void __launch_bounds__(kPkThreads) k_pk_bins(int n, int pc, int nc, const float2* __restrict__ dk,
-                                                        const long long* __restrict__ edges_g, int nbins,
-                                                        double pscale, double kfund, int cic_correct, double shot,
-                                                        double* partials) {
+//
+// The work is split in two.  The bins' geometry (mode count and sum of |m|, exact integers and
+// FP64 square roots) depends only on the mesh and the bin edges: k_pk_geometry computes it once per
+// context and bin count.  The per-call pass k_pk_power only sums |delta_k|^2 (over C2 with
+// cic_correct): FP32 within a warp's run of at most 32 modes, FP64 from the run on.  GB300 has few
+// FP64 units, so the per-mode FP64 square root and FP64 shuffles of a single pass made it
+// FP64-bound (73 ms at 1536^3 against ~2 ms for its 14.5 GB of reads).
+// cic_correct: per mode |delta_k|^2 / C2(m), C2 = prod_i (1 - (2/3) sin^2(pi m_i / n)) the CIC
+// window squared summed over its aliases (Jing 2005 for a locally flat spectrum); the shot noise
+// V / particles is subtracted from the bin mean.
+
+// bin of |m|^2 = m2 among edges[0..nbins] (edges[b] <= m2 < edges[b+1]), -1 outside
+__device__ __forceinline__ int pk_bin_of(long long m2, const long long* edges, int nbins) {
+  if (m2 < edges[0] || m2 >= edges[nbins]) return -1;
+  int lo = 0, hi = nbins;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (m2 >= edges[mid]) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// the half space of §3.3: {kz > 0} U {kz = 0, ky > 0} U {kz = ky = 0, kx > 0}
+__device__ __forceinline__ bool pk_half(int mx, int my, int kz) { return kz > 0 || my > 0 || (my == 0 && mx > 0); }
+
+__global__ void __launch_bounds__(kPkThreads) k_pk_geometry(int n, int nc, const long long* __restrict__ edges_g,
+                                                            int nbins, double* partials) {
   __shared__ long long edges[kMaxBins + 1];
-  __shared__ double hp[kPkWarps][kMaxBins];
   __shared__ double hk[kPkWarps][kMaxBins];
   __shared__ long long hc[kPkWarps][kMaxBins];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int i = threadIdx.x; i <= nbins; i += blockDim.x) edges[i] = edges_g[i];
   for (int i = threadIdx.x; i < kPkWarps * kMaxBins; i += blockDim.x) {
-    (&hp[0][0])[i] = 0.0;
     (&hk[0][0])[i] = 0.0;
     (&hc[0][0])[i] = 0;
   }
@@ -304,46 +323,25 @@ __global__ void __launch_bounds__(kPkThreads) k_pk_bins(int n, int pc, int nc, c
     for (int kz0 = 0; kz0 < nc; kz0 += 32) {
       const int kz = kz0 + lane;
       int bin = -1;
-      double p = 0.0, kk = 0.0;
-      if (kz < nc) {
-        const bool half = kz > 0 || my > 0 || (my == 0 && mx > 0);
+      double kk = 0.0;
+      if (kz < nc && pk_half(mx, my, kz)) {
         const long long m2 = (long long)mx * mx + (long long)my * my + (long long)kz * kz;
-        if (half && m2 >= edges[0] && m2 < edges[nbins]) {
-          int lo = 0, hi = nbins;   // edges[lo] <= m2 < edges[hi]
-          while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (m2 >= edges[mid]) lo = mid; else hi = mid;
-          }
-          bin = lo;
-          const float2 z = dk[row * pc + kz];
-          p = ((double)z.x * z.x + (double)z.y * z.y) * pscale;
-          if (cic_correct) {
-            const double sx = sin(M_PI * mx / n), sy = sin(M_PI * my / n), sz = sin(M_PI * kz / n);
-            const double c2 = (1.0 - (2.0 / 3.0) * sx * sx) * (1.0 - (2.0 / 3.0) * sy * sy) *
-                              (1.0 - (2.0 / 3.0) * sz * sz);
-            p = p / c2 - shot;
-          }
-          kk = sqrt((double)m2) * kfund;
-        }
+        bin = pk_bin_of(m2, edges, nbins);
+        if (bin >= 0) kk = sqrt((double)m2);
       }
-      // segmented inclusive scan over runs of equal bins (bins never decrease along a row), in a
-      // fixed shuffle order; the last lane of each run adds the run's sums to the histogram
       long long c = bin >= 0 ? 1 : 0;
 #pragma unroll
       for (int d = 1; d < 32; d <<= 1) {
         const int ob = __shfl_up_sync(0xffffffffu, bin, d);
-        const double op = __shfl_up_sync(0xffffffffu, p, d);
         const double ok = __shfl_up_sync(0xffffffffu, kk, d);
         const long long oc = __shfl_up_sync(0xffffffffu, c, d);
         if (lane >= d && ob == bin) {
-          p += op;
           kk += ok;
           c += oc;
         }
       }
       const int nb_next = __shfl_down_sync(0xffffffffu, bin, 1);
       if (bin >= 0 && (lane == 31 || nb_next != bin)) {
-        hp[warp][bin] += p;
         hk[warp][bin] += kk;
         hc[warp][bin] += c;
       }
@@ -352,31 +350,112 @@ __global__ void __launch_bounds__(kPkThreads) k_pk_bins(int n, int pc, int nc, c
   }
   __syncthreads();
   for (int b = threadIdx.x; b < nbins; b += blockDim.x) {
-    double sp = 0.0, sk = 0.0;
+    double sk = 0.0;
     long long sc = 0;
     for (int w = 0; w < kPkWarps; ++w) {
-      sp += hp[w][b];
       sk += hk[w][b];
       sc += hc[w][b];
     }
-    double* out = partials + (size_t)blockIdx.x * 3 * nbins;
+    double* out = partials + (size_t)blockIdx.x * 2 * nbins;
     out[b] = sk;
-    out[nbins + b] = sp;
-    out[2 * nbins + b] = (double)sc;
+    out[nbins + b] = (double)sc;
   }
 }
 
-__global__ void k_pk_finish(const double* __restrict__ partials, int nblocks, int nbins, double* pk) {
+// geom[0..nbins) = sum of |m| per bin, geom[nbins..2 nbins) = mode count (exact in FP64)
+__global__ void k_pk_geometry_finish(const double* __restrict__ partials, int nblocks, int nbins, double* geom) {
   for (int b = threadIdx.x; b < nbins; b += blockDim.x) {
-    double sk = 0.0, sp = 0.0, sc = 0.0;
+    double sk = 0.0, sc = 0.0;
     for (int i = 0; i < nblocks; ++i) {
-      const double* in = partials + (size_t)i * 3 * nbins;
-      sk += in[b];
-      sp += in[nbins + b];
-      sc += in[2 * nbins + b];
+      sk += partials[(size_t)i * 2 * nbins + b];
+      sc += partials[(size_t)i * 2 * nbins + nbins + b];
     }
-    pk[b] = sc > 0 ? sk / sc : 0.0;
-    pk[nbins + b] = sc > 0 ? sp / sc : 0.0;
+    geom[b] = sk;
+    geom[nbins + b] = sc;
+  }
+}
+
+constexpr int kPkUnroll = 4;   // k_z chunks of 32 whose loads a lane issues before scanning them
+
+__global__ void __launch_bounds__(kPkThreads) k_pk_power(int n, int pc, int nc, const float2* __restrict__ dk,
+                                                         const long long* __restrict__ edges_g, int nbins,
+                                                         int cic_correct, double* partials) {
+  __shared__ long long edges[kMaxBins + 1];
+  __shared__ double hp[kPkWarps][kMaxBins];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i <= nbins; i += blockDim.x) edges[i] = edges_g[i];
+  for (int i = threadIdx.x; i < kPkWarps * kMaxBins; i += blockDim.x) (&hp[0][0])[i] = 0.0;
+  __syncthreads();
+  const long long nrows = (long long)n * n;
+  const float inv_n = 1.0f / (float)n;
+  for (long long row = (long long)blockIdx.x * kPkWarps + warp; row < nrows;
+       row += (long long)gridDim.x * kPkWarps) {
+    const int mx = signed_mode((int)(row / n), n), my = signed_mode((int)(row % n), n);
+    const long long mxy = (long long)mx * mx + (long long)my * my;
+    float cxy = 1.0f;
+    if (cic_correct) {
+      const float sx = sinpif((float)mx * inv_n), sy = sinpif((float)my * inv_n);
+      cxy = (1.0f - (2.0f / 3.0f) * sx * sx) * (1.0f - (2.0f / 3.0f) * sy * sy);
+    }
+    const float2* rowp = dk + row * pc;
+    int bin = -2;   // the lane's current bin along the row (-2: not searched yet)
+    for (int kz0 = 0; kz0 < nc; kz0 += 32 * kPkUnroll) {
+      // the chunk's loads first (streaming: the spectrum is read once), then one scan per 32 modes
+      float2 z[kPkUnroll];
+#pragma unroll
+      for (int u = 0; u < kPkUnroll; ++u) {
+        const int kz = kz0 + 32 * u + lane;
+        z[u] = kz < nc ? __ldcs(rowp + kz) : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < kPkUnroll; ++u) {
+        const int kz = kz0 + 32 * u + lane;
+        int b = -1;
+        float p = 0.0f;
+        if (kz < nc && pk_half(mx, my, kz)) {
+          const long long m2 = mxy + (long long)kz * kz;
+          // |m|^2 grows along the row: advance the previous bin instead of searching again
+          if (bin < 0 || m2 < edges[bin]) bin = pk_bin_of(m2, edges, nbins);
+          else
+            while (bin >= 0 && m2 >= edges[bin + 1]) bin = bin + 1 < nbins ? bin + 1 : -1;
+          b = bin;
+          if (b >= 0) {
+            p = z[u].x * z[u].x + z[u].y * z[u].y;
+            if (cic_correct) {
+              const float sz = sinpif((float)kz * inv_n);
+              p = p / (cxy * (1.0f - (2.0f / 3.0f) * sz * sz));
+            }
+          }
+        }
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+          const int ob = __shfl_up_sync(0xffffffffu, b, d);
+          const float op = __shfl_up_sync(0xffffffffu, p, d);
+          if (lane >= d && ob == b) p += op;
+        }
+        const int nb_next = __shfl_down_sync(0xffffffffu, b, 1);
+        if (b >= 0 && (lane == 31 || nb_next != b)) hp[warp][b] += (double)p;
+        __syncwarp();
+      }
+    }
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < nbins; b += blockDim.x) {
+    double sp = 0.0;
+    for (int w = 0; w < kPkWarps; ++w) sp += hp[w][b];
+    partials[(size_t)blockIdx.x * nbins + b] = sp;
+  }
+}
+
+// pk[0..nbins) = mean |k| (h/Mpc), pk[nbins..) = P = pscale * mean power - shot, pk[2 nbins..) = modes
+__global__ void k_pk_finish(const double* __restrict__ partials, int nblocks, int nbins,
+                            const double* __restrict__ geom, double kfund, double pscale, double shot, double* pk) {
+  for (int b = threadIdx.x; b < nbins; b += blockDim.x) {
+    double sp = 0.0;
+    for (int i = 0; i < nblocks; ++i) sp += partials[(size_t)i * nbins + b];
+    const double sk = geom[b], sc = geom[nbins + b];
+    pk[b] = sc > 0 ? sk / sc * kfund : 0.0;
+    pk[nbins + b] = sc > 0 ? pscale * sp / sc - shot : 0.0;
     pk[2 * nbins + b] = sc;
   }
 }
@@ -469,15 +548,22 @@ int launch_snapshot(long long npart, const float* s, const float* v, const float
   return check_launch("snapshot");
 }
 
-int launch_pk_bins(const Grid3& g, const float2* dk, const long long* edges, int nbins, double pscale, double kfund,
-                   int cic_correct, double shot, double* partials, int nblocks, cudaStream_t st) {
-  k_pk_bins<<<nblocks, kPkThreads, 0, st>>>(g.n, g.pc, g.nc, dk, edges, nbins, pscale, kfund, cic_correct, shot,
-                                             partials);
+int launch_pk_geometry(const Grid3& g, const long long* edges, int nbins, double* partials, int nblocks,
+                       double* geom, cudaStream_t st) {
+  k_pk_geometry<<<nblocks, kPkThreads, 0, st>>>(g.n, g.nc, edges, nbins, partials);
+  k_pk_geometry_finish<<<1, 128, 0, st>>>(partials, nblocks, nbins, geom);
+  return check_launch("pk_geometry");
+}
+
+int launch_pk_bins(const Grid3& g, const float2* dk, const long long* edges, int nbins, int cic_correct,
+                   double* partials, int nblocks, cudaStream_t st) {
+  k_pk_power<<<nblocks, kPkThreads, 0, st>>>(g.n, g.pc, g.nc, dk, edges, nbins, cic_correct, partials);
   return check_launch("pk_bins");
 }
 
-int launch_pk_finish(const double* partials, int nblocks, int nbins, double* pk, cudaStream_t st) {
-  k_pk_finish<<<1, 256, 0, st>>>(partials, nblocks, nbins, pk);
+int launch_pk_finish(const double* partials, int nblocks, int nbins, const double* geom, double kfund, double pscale,
+                     double shot, double* pk, cudaStream_t st) {
+  k_pk_finish<<<1, 128, 0, st>>>(partials, nblocks, nbins, geom, kfund, pscale, shot, pk);
   return check_launch("pk_finish");
 }
 
