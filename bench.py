@@ -17,6 +17,7 @@ the data path): weak scaling, replicas only.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import hashlib
 import json
 import math
@@ -144,30 +145,204 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-# ---- CPU oracle sample -----------------------------------------------------------------------------
-def oracle_sample_step(repeats: int = 1):
-    """Time one FP64 oracle COLA step on SAMPLE; returns (seconds per step, particles)."""
+# ---- CPU oracle baseline (the FP64 oracle as it stands, on the host cores) ----------------------
+# The oracle is plain single-threaded numpy; it uses the host's cores through independent replicas
+# (one process per core, each its own realisation), the same parallelism as the GPU arm's replicas.
+# Processes are started with `spawn` (never forked from a process that has touched the GPU).
+CPU_CONFIGS = {
+    "32^3/64^3": dict(box=256.0, np_side=32, nmesh=64, seed=1),      # the small parity workload
+    "256^3/512^3": dict(box=600.0, np_side=256, nmesh=512, seed=2),  # the medium workload
+}
+ORACLE_BYTES_PER_MESH_CELL = 90.0   # peak host memory of one oracle step per mesh cell (11.3 GB at 512^3)
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def host_available_bytes() -> float:
+    try:
+        with open("/proc/meminfo") as fh:
+            for line in fh:
+                if line.startswith("MemAvailable:"):
+                    return float(line.split()[1]) * 1024.0
+    except OSError:
+        pass
+    return 16e9
+
+
+def _oracle_worker(conn, w, seed):
+    """One oracle replica: set up its realisation, then one timed COLA step per request."""
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
     import oracle
-    from oracle import cola, lpt
-    p = oracle.Params(box=SAMPLE["box"], np_side=SAMPLE["np_side"], nmesh=SAMPLE["nmesh"])
-    wn = cola_inputs.white_noise(SAMPLE["np_side"], SAMPLE["seed"])
-    psi1, psi2 = lpt.displacements(wn, p)
+    from oracle import cola, lpt, rng
+    p = oracle.Params(box=w["box"], np_side=w["np_side"], nmesh=w["nmesh"])
+    psi1, psi2 = lpt.displacements(rng.white_noise(seed, p.np_side), p)
     s, v = cola.initial_state(psi1, psi2, p)
-    times = []
-    for r in range(repeats):
+    i = 0
+    conn.send("ready")
+    while conn.recv() == "step":
         t0 = time.perf_counter()
-        s, v = cola.step(1 + r % p.nstep, s, v, psi1, psi2, p)
-        times.append(time.perf_counter() - t0)
-    return times, SAMPLE["np_side"] ** 3
+        s, v = cola.step(1 + i % p.nstep, s, v, psi1, psi2, p)
+        conn.send(time.perf_counter() - t0)
+        i += 1
+
+
+class OracleReplicas:
+    """`procs` oracle processes, each holding one realisation of workload w; step() advances them
+    all by one COLA step concurrently and returns the wall time."""
+
+    def __init__(self, w, procs: int):
+        import multiprocessing as mp
+        ctx = mp.get_context("spawn")
+        self.conns, self.procs = [], []
+        for r in range(procs):
+            a, b = ctx.Pipe()
+            pr = ctx.Process(target=_oracle_worker, args=(b, w, w["seed"] + 1000 * r), daemon=True)
+            pr.start()
+            self.conns.append(a)
+            self.procs.append(pr)
+        for c in self.conns:
+            c.recv()
+
+    def step(self) -> float:
+        t0 = time.perf_counter()
+        for c in self.conns:
+            c.send("step")
+        for c in self.conns:
+            c.recv()
+        return time.perf_counter() - t0
+
+    def close(self):
+        for c in self.conns:
+            c.send("stop")
+        for pr in self.procs:
+            pr.join(timeout=30)
+
+
+def oracle_procs_for(w, cores: int) -> int:
+    """Replicas that fit: one per core, at most what half the available host memory holds."""
+    per = ORACLE_BYTES_PER_MESH_CELL * w["nmesh"] ** 3
+    return max(1, min(cores, int(0.5 * host_available_bytes() // per)))
+
+
+def _oracle_parts_job(w):
+    """Seconds of the particle work (deposit, interpolation) and of the mesh work (FFTs, Green
+    function) of one oracle PM force at workload w, from the oracle's own functions."""
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    import oracle
+    from oracle import cic, cola, lpt, pm, rng
+    p = oracle.Params(box=w["box"], np_side=w["np_side"], nmesh=w["nmesh"])
+    psi1, psi2 = lpt.displacements(rng.white_noise(w["seed"], p.np_side), p)
+    s, _ = cola.initial_state(psi1, psi2, p)
+    t0 = time.perf_counter()
+    delta = pm.density_fixed(s, p.np_side, p.nmesh)
+    t1 = time.perf_counter()
+    f = pm.force_mesh(delta, 1.0)
+    t2 = time.perf_counter()
+    cell, w1 = cic.interp_weights_fixed(s, p.np_side, p.nmesh)
+    cic.cic_interp(f, cell, w1)
+    t3 = time.perf_counter()
+    return {"particle_s": (t1 - t0) + (t3 - t2), "mesh_s": t2 - t1}
+
+
+def _oracle_realisation_job(w):
+    """Seconds of one oracle realisation's parts at workload w: 2LPT, one COLA step, one P(k)."""
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    import oracle
+    from oracle import cola, lpt, pm, power, rng
+    p = oracle.Params(box=w["box"], np_side=w["np_side"], nmesh=w["nmesh"])
+    t0 = time.perf_counter()
+    psi1, psi2 = lpt.displacements(rng.white_noise(w["seed"], p.np_side), p)
+    t1 = time.perf_counter()
+    s, v = cola.initial_state(psi1, psi2, p)
+    s, v = cola.step(1, s, v, psi1, psi2, p)
+    t2 = time.perf_counter()
+    power.power_spectrum(pm.density_fixed(s, p.np_side, p.nmesh), p.box, 64)
+    t3 = time.perf_counter()
+    return {"ic_s": t1 - t0, "step_s": t2 - t1, "pk_s": t3 - t2}
+
+
+def _oracle_adjoint_job(args):
+    """Seconds of the oracle's forward (2LPT + 10 steps, continuous CIC) or forward + adjoint."""
+    w, ngrid, which = args
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    import numpy as np
+    import oracle
+    from oracle import adjoint, rng
+    p = oracle.Params(box=w["box"], np_side=w["np_side"], nmesh=w["nmesh"])
+    wn = rng.white_noise(w["seed"], p.np_side)
+    t0 = time.perf_counter()
+    if which == "forward":
+        adjoint.forward(wn, p)
+    else:
+        adjoint.gradient(wn, p, ngrid, np.zeros((ngrid,) * 3))
+    return time.perf_counter() - t0
 
 
 def cpu_baseline_entry():
-    times, npart = oracle_sample_step(1)
-    t = times[0]
-    return {"value": npart / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": (f"one FP64 oracle COLA step (numpy, single thread) on {SAMPLE['np_side']}^3 particles / "
-                       f"{SAMPLE['nmesh']}^3 mesh, L={SAMPLE['box']:g} Mpc/h: the large workload's cell size and "
-                       f"particle spacing in a smaller box; {t:.2f} s")}
+    """The FP64 oracle on the host cores: particle-steps/s per PM step at 32^3/64^3 and 256^3/512^3
+    (one replica per core, within host memory), the 1024^3/1536^3 rate extrapolated from the
+    256^3/512^3 step, and CPU estimates of the batched mocks/hour and the adjoint/forward cost.  The
+    side measurements (six processes) run beside the 256^3/512^3 replicas, on cores of their own."""
+    import multiprocessing as mp
+    cores = host_cores()
+    out = {"kind": "oracle", "unit": UNIT, "cores": cores, "nproc": cores}
+    rates = {}
+    small = CPU_CONFIGS["32^3/64^3"]
+    procs = oracle_procs_for(small, cores)
+    reps = OracleReplicas(small, procs)
+    t = min(reps.step() for _ in range(3))
+    reps.close()
+    rates["32^3/64^3"] = {"value": procs * small["np_side"] ** 3 / t, "processes": procs, "step_wall_s": t}
+    med = CPU_CONFIGS["256^3/512^3"]
+    side = 6
+    mem_slots = int(0.5 * host_available_bytes() // (ORACLE_BYTES_PER_MESH_CELL * med["nmesh"] ** 3))
+    procs = max(1, min(cores - side, mem_slots - 1))
+    with mp.get_context("spawn").Pool(side) as pool:
+        parts_r = pool.apply_async(_oracle_parts_job, (med,))
+        shapes = [dict(box=300.0, np_side=96, nmesh=192, seed=100), dict(box=400.0, np_side=128, nmesh=256, seed=124),
+                  dict(box=500.0, np_side=160, nmesh=320, seed=148)]
+        real_r = [pool.apply_async(_oracle_realisation_job, (w,)) for w in shapes]
+        adj_w = dict(box=200.0, np_side=64, nmesh=128, seed=4)   # the differentiable workload's cell, 1/8 volume
+        fwd_r = pool.apply_async(_oracle_adjoint_job, ((adj_w, 32, "forward"),))
+        grad_r = pool.apply_async(_oracle_adjoint_job, ((adj_w, 32, "gradient"),))
+        reps = OracleReplicas(med, procs)
+        t = reps.step()
+        reps.close()
+        rates["256^3/512^3"] = {"value": procs * med["np_side"] ** 3 / t, "processes": procs, "step_wall_s": t}
+        parts = parts_r.get()
+        reals = [r.get() for r in real_r]
+        fwd_s, grad_s = fwd_r.get(), grad_r.get()
+    # 1024^3 / 1536^3: the particle work scales with n, the mesh work with N^3 log N^3
+    n1, N1, n2, N2 = med["np_side"] ** 3, med["nmesh"], 1024 ** 3, 1536
+    step1 = rates["256^3/512^3"]["step_wall_s"]
+    other = max(step1 - parts["particle_s"] - parts["mesh_s"], 0.0)
+    mesh_scale = (N2 ** 3 * math.log2(N2 ** 3)) / (N1 ** 3 * math.log2(N1 ** 3))
+    t_large = (parts["particle_s"] + other) * n2 / n1 + parts["mesh_s"] * mesh_scale
+    # CPU mocks/hour: realisation = 2LPT + 10 steps + P(k) per shape, the 64-member mix over all cores
+    per_shape = [r["ic_s"] + 10.0 * r["step_s"] + r["pk_s"] for r in reals]
+    batch_cpu_s = 24 * per_shape[0] + 24 * per_shape[1] + 16 * per_shape[2]
+    out.update({
+        "value": rates["256^3/512^3"]["value"],
+        "sample": ("FP64 numpy oracle, one COLA step per replica process, one replica per core within host memory: "
+                   "value = 256^3 particles / 512^3 mesh (600 Mpc/h), processes in by_config"),
+        "by_config": rates,
+        "large_extrapolated": {"value": cores * n2 / t_large, "seconds_per_step_one_core": t_large,
+                               "note": "extrapolated, not run: 1024^3/1536^3 needs ~300 GB of FP64 meshes; particle "
+                                       "work scaled by n, mesh work by N^3 log N^3 from the 256^3/512^3 step, all cores "
+                                       "as independent replicas"},
+        "batched_mocks_per_hour_estimated": 64 * 3600.0 * cores / batch_cpu_s,
+        "batched_note": "estimated from one timed 2LPT, COLA step and P(k) per shape (96^3/192^3, 128^3/256^3, "
+                        "160^3/320^3); realisation = 2LPT + 10 steps + P(k); 64-member mix over all cores",
+        "adjoint_over_forward": (grad_s - fwd_s) / fwd_s,
+        "adjoint_note": "oracle forward (2LPT + 10 steps) vs forward + hand-written adjoint, 64^3/128^3 in 200 Mpc/h "
+                        "(the differentiable workload's cell), loss on a 32^3 grid",
+    })
+    return out
 
 
 def run_reference(args):
@@ -175,16 +350,22 @@ def run_reference(args):
     if rank != 0:
         return 0
     w = WORKLOADS[args.workload]
-    times, npart = oracle_sample_step(args.warmup + args.steps)
-    timed = times[args.warmup:]
+    cores = host_cores()
+    procs = oracle_procs_for(SAMPLE, cores)
+    reps = OracleReplicas(SAMPLE, procs)
+    for _ in range(args.warmup):
+        reps.step()
+    timed = [reps.step() for _ in range(args.steps)]
+    reps.close()
     t = sum(timed) / len(timed)
-    value = npart / t
+    value = procs * SAMPLE["np_side"] ** 3 / t
+    sample = (f"{procs} FP64 oracle replicas (one process per core), one COLA step each per step, on "
+              f"{describe(SAMPLE)}: the large workload's cell size and particle spacing in a smaller box")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": describe(w), "timed_sample": describe(SAMPLE)},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"one FP64 oracle COLA step per step on {describe(SAMPLE)}"},
+            "config": {"workload": describe(w), "timed_sample": describe(SAMPLE), "nproc": cores},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": procs, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -224,12 +405,13 @@ def measure_adjoint(args, torch, device):
     from paper_1507_05329_gb300 import Context, Params
     wl = cola_inputs.WORKLOADS["adjoint"]
     cfg = cola_inputs.ADJOINT_LOSS
-    p = Params(box=wl["box"], np_side=wl["np_side"], nmesh=wl["nmesh"], nstep=10)
+    from paper_1507_05329_gb300 import binding
+    p = Params(box=wl["box"], np_side=wl["np_side"], nmesh=wl["nmesh"], nstep=10, seed=wl["seed"])
     stream = torch.cuda.current_stream()
     ctx = Context(p, stream)
     ng = cfg["ngrid"]
-    wn = cola_inputs.white_noise_torch(p.np_side, wl["seed"], device)
-    tgt = ctx.grid_density(ctx.run(cola_inputs.white_noise_torch(p.np_side, cfg["target_seed"], device),
+    wn = binding.white_noise(p)                                   # the library's seeded field
+    tgt = ctx.grid_density(ctx.run(binding.white_noise(dataclasses.replace(p, seed=cfg["target_seed"])),
                                    with_pk=False)["s"], ng)
     out = {k: ctx.empty_particles() for k in ("s", "v", "psi1", "psi2")}
 
@@ -278,8 +460,9 @@ def measure_batched(args, torch, device):
     set (about 30 GB) exceeds L2."""
     from paper_1507_05329_gb300 import Batch, Context, Params
     members = cola_inputs.batched_workload()
-    params = [Params(box=m["box"], np_side=m["np_side"], nmesh=m["nmesh"], nstep=10) for m in members]
-    wns = [cola_inputs.white_noise_torch(p.np_side, m["seed"], device) for p, m in zip(params, members)]
+    params = [Params(box=m["box"], np_side=m["np_side"], nmesh=m["nmesh"], nstep=10, seed=m["seed"]) for m in members]
+    from paper_1507_05329_gb300 import binding
+    fields = [binding.white_noise(p) for p in params]   # the plain loop's inputs: each member's seeded field
     stream = torch.cuda.current_stream()
     k = max(args.steps, 2)
 
@@ -304,7 +487,7 @@ def measure_batched(args, torch, device):
         o["pk"] = torch.empty((3, 64), dtype=torch.float64, device=device)
 
     def plain():
-        for p, w in zip(params, wns):
+        for p, w in zip(params, fields):
             key = (p.np_side, p.nmesh, p.box)
             ctxs[key].run(w, 64, out=outs[key])
 
@@ -315,7 +498,9 @@ def measure_batched(args, torch, device):
     del ctxs, outs
     torch.cuda.empty_cache()
 
-    batch = Batch(params, wns, nbins=64, nstreams=args.lanes, stream=stream)
+    del fields
+    # batched: every member draws the field of its own seed inside its cola_run (white noise None)
+    batch = Batch(params, [None] * len(params), nbins=64, nstreams=args.lanes, stream=stream)
     batch.run(use_graph=False)
     batch.sync()
     batch.tune(reps=5)          # force evaluations of 1-3 ms: more repetitions than the large workload's 2
@@ -350,11 +535,11 @@ def run_ours(args):
     build.build()
     w = WORKLOADS[args.workload]
     seed = replica_seed(w["seed"], rank)
-    p = Params(box=w["box"], np_side=w["np_side"], nmesh=w["nmesh"], nstep=10)
+    p = Params(box=w["box"], np_side=w["np_side"], nmesh=w["nmesh"], nstep=10, seed=seed)
     n = p.n
     stream = torch.cuda.current_stream()
     ctx = Context(p, stream)
-    wn = cola_inputs.white_noise_torch(p.np_side, seed, f"cuda:{local}")
+    wn = None          # each realisation draws the field of its seed (Philox-4x32-10) inside cola_run
     out = {k: ctx.empty_particles() for k in ("s", "v", "psi1", "psi2")}
     out["pk"] = torch.empty((3, args.nbins), dtype=torch.float64, device=f"cuda:{local}")
 
@@ -397,6 +582,13 @@ def run_ours(args):
     if ws > 1:
         ms = slowest_rank_ms(ms, dist, f"cuda:{local}")
     value = whole_job_rate(ws, n, p.nstep, ms)
+    me = {"rank": rank, "local_rank": local, "device": torch.cuda.get_device_name(local),
+          "pci_bus_id": torch.cuda.get_device_properties(local).pci_bus_id if hasattr(
+              torch.cuda.get_device_properties(local), "pci_bus_id") else None}
+    rank_devices = [me]
+    if ws > 1:
+        rank_devices = [None] * ws
+        dist.all_gather_object(rank_devices, me)
 
     # roofline of the dominant PM-step kernel
     sb = stage_bytes(p.nmesh, n)
@@ -436,12 +628,13 @@ def run_ours(args):
     # when the last result has reached the host.
     e2e = None
     if args.e2e_steps > 0:
+        # the user-supplied-field path of the public API: the seed's field travels from host memory
         wn_host = torch.empty(n, dtype=torch.float32, pin_memory=True)
-        wn_host.copy_(wn.cpu())
+        wn_host.copy_(binding.white_noise(p).cpu())
         s_host = torch.empty((3, n), dtype=torch.float32, pin_memory=True)
         v_host = torch.empty((3, n), dtype=torch.float32, pin_memory=True)
         pk_host = torch.empty((3, args.nbins), dtype=torch.float64, pin_memory=True)
-        wn_dev = [torch.empty_like(wn) for _ in range(2)]
+        wn_dev = [torch.empty(n, dtype=torch.float32, device=f"cuda:{local}") for _ in range(2)]
         outs = [out, {"s": ctx.empty_particles(), "v": ctx.empty_particles(), "psi1": out["psi1"],
                       "psi2": out["psi2"], "pk": torch.empty_like(out["pk"])}]
         copy = torch.cuda.Stream()
@@ -485,7 +678,7 @@ def run_ours(args):
 
     ctx.sync()
     ctx.close()
-    del out, wn
+    del out
     torch.cuda.empty_cache()
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -501,7 +694,8 @@ def run_ours(args):
                 "vs_baseline": None, "dtype": "f32 (int64 fixed-point deposit)", "data": "synthetic",
                 "config": {"workload": describe(w), "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                            "l2": "inputs larger than L2 (no flush needed)",
-                           "pm_step_ms": pm_ms / 10.0, "nbins": args.nbins, "autotune": tuned},
+                           "pm_step_ms": pm_ms / 10.0, "nbins": args.nbins, "autotune": tuned,
+                           "rank_devices": rank_devices},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clocks, "stages": per_stage, "adjoint": adj, "batched": batched}
         print(json.dumps(line), flush=True)
@@ -527,10 +721,44 @@ def main():
                     help="keep the size-based default schedule instead of timing the candidates first")
     ap.add_argument("--schedule", type=int, default=None,
                     help="run every realisation (warm-up included) under this cola_set_schedule value, untuned")
+    ap.add_argument("--launch-check", action="store_true",
+                    help="start the ranks (gloo, no GPU work) and print which ranks came up; no measurement")
     args = ap.parse_args()
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        return launch_ranks(args.gpus)
+    if args.launch_check:
+        return launch_check(args)
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     return run_reference(args) if args.impl == "reference" else run_ours(args)
+
+
+def launch_ranks(n: int) -> int:
+    """`bench.py --gpus N` started by hand: re-run this command as N local ranks (one per GPU) under
+    torch.distributed.run on 127.0.0.1; rank 0 prints the line."""
+    import socket
+    with socket.socket(socket.AF_INET, socket.SOCK_STREAM) as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={n}",
+           "--master-addr=127.0.0.1", f"--master-port={port}", os.path.abspath(__file__), *sys.argv[1:]]
+    return subprocess.call(cmd)
+
+
+def launch_check(args) -> int:
+    """Every rank joins a gloo group and reports (rank, local rank, world); rank 0 prints them."""
+    import torch.distributed as dist
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("gloo")
+        got = [None] * ws
+        dist.all_gather_object(got, {"rank": rank, "local_rank": local, "pid": os.getpid()})
+        dist.destroy_process_group()
+    else:
+        got = [{"rank": rank, "local_rank": local, "pid": os.getpid()}]
+    if rank == 0:
+        print(json.dumps({"launch_check": True, "n_gpus": ws, "ranks": got}), flush=True)
+    return 0
 
 
 if __name__ == "__main__":

@@ -63,6 +63,7 @@ typedef struct {
     int ic_mode;          /* 0: eq. (initial_time), v_res = 0 at a_{1/2};
                              1: Appendix A eq. (initial_time_original), v_res = 0 at a_1 */
     int drift_ansatz;     /* 0: eq. (ansatz-drift); 1: v_res constant during a drift (§2.1) */
+    unsigned long long seed;  /* seed of the white noise drawn when a call gets white_noise == NULL */
 } cola_params;
 
 typedef struct cola_ctx cola_ctx;
@@ -100,8 +101,23 @@ int cola_step_scalars(const cola_params* params, int i, double* out, int nout);
  * Returns COLA_ERR_INVALID for invalid parameters or a negative or non-finite k. */
 int cola_linear_power(const cola_params* params, const double* k, int nk, double* power, double* transfer);
 
+/* Seeded white noise (§2.3: the initial conditions are Gaussian random modes drawn from a seed; the
+ * paper does not name its generator).  One unit Gaussian per lattice site, from the counter-based
+ * generator Philox-4x32-10 (Salmon, Moraes, Dror & Shaw 2011) and the Box-Muller transform: site i
+ * (particle id) takes counter j = i/4 = (j mod 2^32, j div 2^32, 0, 0) under key (seed mod 2^32,
+ * seed div 2^32); output words (x0, x1) give sites 4j, 4j+1 and (x2, x3) sites 4j+2, 4j+3 as
+ * (r cos 2 pi u2, r sin 2 pi u2), r = sqrt(-2 ln u1), u1 = ((a >> 8) + 1) 2^-24, u2 = (b >> 8) 2^-24,
+ * evaluated in FP32.  The field is a pure function of (seed, i).
+ * cola_white_noise writes params->seed's field to out (device float32 [np^3]) on `stream`
+ * (cudaStream_t); only np and seed are used (params must still be valid).
+ * cola_philox_words writes the raw words of counters first .. first+count-1 under `seed` to out
+ * (device uint32 [count][4]).  Both are asynchronous; COLA_ERR_INVALID for bad arguments. */
+int cola_white_noise(const cola_params* params, float* out, void* stream);
+int cola_philox_words(unsigned long long seed, long long first, long long count, unsigned* out, void* stream);
+
 /* S0 — 2LPT initial conditions (§2.1 growing mode; §2.3 2LPTic-style Gaussian modes).
- * white_noise: device float32 [n], unit Gaussian, one value per lattice site (input).
+ * white_noise: device float32 [n], unit Gaussian, one value per lattice site (input), or NULL to
+ * draw the field of params.seed (cola_white_noise) inside the call.
  * Writes psi1, psi2, s = D1(a_1) Psi1 + D2(a_1) Psi2 and v = 0 (eq. initial_time). */
 int cola_ic_2lpt(cola_ctx* ctx, const float* white_noise, float* s, float* v,
                  float* psi1, float* psi2);
@@ -128,8 +144,9 @@ int cola_pm_force(cola_ctx* ctx, const float* s, double a, float* force);
  * 2LPT growth increments.  The last step kicks to a_nstep and does not drift.  In place on s, v. */
 int cola_step(cola_ctx* ctx, int i, float* s, float* v, const float* psi1, const float* psi2);
 
-/* A whole realisation: cola_ic_2lpt, then steps 1..nstep, then (if pk != NULL) the power
- * spectrum of the final positions into pk (device double [3][nbins]). */
+/* A whole realisation: cola_ic_2lpt (white_noise NULL: the field of params.seed), then steps
+ * 1..nstep, then (if pk != NULL) the power spectrum of the final positions into pk (device double
+ * [3][nbins]). */
 int cola_run(cola_ctx* ctx, const float* white_noise, float* s, float* v, float* psi1,
              float* psi2, double* pk, int nbins);
 
@@ -224,7 +241,7 @@ int cola_run_checkpointed(cola_ctx* ctx, const float* white_noise, float* s, flo
 
 /* Vector-Jacobian product of cola_run_checkpointed with respect to the white noise.
  *   white_noise : the same device float32 [np^3] input as the forward (the 2LPT Hessians are
- *                 recomputed from it).
+ *                 recomputed from it), or NULL if the forward drew the field of params.seed.
  *   ckpt        : the forward's checkpoints; the PM force of each step is recomputed from them.
  *   lam_s       : cotangent of the final s, device float32 [3][np^3] (required).
  *   lam_v, lam_psi1, lam_psi2 : cotangents of the final v_res, Psi1 and Psi2 (device float32
@@ -259,8 +276,9 @@ int cola_grid_density_adjoint(cola_ctx* ctx, const float* s, int ngrid, const fl
  *   use_graph = 1 : the first call runs once eagerly (warm-up, then synchronises), captures the
  *                   whole launch sequence into a CUDA graph and launches it; later calls only
  *                   launch the graph (one host call for all realisations).
- * io[i] holds realisation i's device buffers (as for cola_run: white noise [np^3], s, v, psi1,
- * psi2 [3][np^3] float32, pk double [3][nbins]); all 16-byte aligned, caller-owned, fixed for the
+ * io[i] holds realisation i's device buffers (as for cola_run: white noise [np^3] or NULL for the
+ * field of params[i].seed, s, v, psi1, psi2 [3][np^3] float32, pk double [3][nbins]); all 16-byte
+ * aligned, caller-owned, fixed for the
  * batch's lifetime (the graph records the pointers).  params[i] is realisation i's parameters
  * (sizes may differ).  Contexts hold their own meshes: the batch needs the sum of the members'
  * context memory.  All calls are asynchronous on `stream` except create, sync and tune.

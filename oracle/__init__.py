@@ -14,5 +14,5 @@ Units: H0 = 1, lengths of the particle/mesh arrays in PM mesh cells (L / N), the
 variable is the scale factor a, velocities are canonical (v = a^2 dx/dt).
 """
 
-from . import cosmology, cic, fourier, pm, lpt, power, cola, adjoint, fof  # noqa: F401
+from . import cosmology, cic, fourier, pm, lpt, power, cola, adjoint, fof, rng  # noqa: F401
 from .cosmology import Params  # noqa: F401

@@ -29,7 +29,7 @@ class CParams(ctypes.Structure):
     _fields_ = [("omega_m", ctypes.c_double), ("h", ctypes.c_double), ("n_s", ctypes.c_double),
                 ("sigma8", ctypes.c_double), ("box", ctypes.c_double), ("np", ctypes.c_int),
                 ("nmesh", ctypes.c_int), ("nstep", ctypes.c_int), ("nlpt", ctypes.c_double),
-                ("ic_mode", ctypes.c_int), ("drift_ansatz", ctypes.c_int)]
+                ("ic_mode", ctypes.c_int), ("drift_ansatz", ctypes.c_int), ("seed", ctypes.c_ulonglong)]
 
 
 @dataclasses.dataclass(frozen=True)
@@ -47,6 +47,7 @@ class Params:
     nlpt: float = -2.5
     ic_mode: int = 0
     drift_ansatz: int = 0
+    seed: int = 0           # white noise of calls given white_noise=None
 
     @property
     def n(self) -> int:
@@ -54,7 +55,7 @@ class Params:
 
     def to_c(self) -> CParams:
         return CParams(self.omega_m, self.h, self.n_s, self.sigma8, self.box, self.np_side, self.nmesh,
-                       self.nstep, self.nlpt, self.ic_mode, self.drift_ansatz)
+                       self.nstep, self.nlpt, self.ic_mode, self.drift_ansatz, self.seed)
 
 
 _LIB = None
@@ -66,6 +67,8 @@ SIGNATURES = {
     "cola_sync": ([_VP], _I),
     "cola_strerror": ([_I], ctypes.c_char_p),
     "cola_step_scalars": ([ctypes.POINTER(CParams), _I, ctypes.POINTER(_D), _I], _I),
+    "cola_white_noise": ([ctypes.POINTER(CParams), _VP, _VP], _I),
+    "cola_philox_words": ([ctypes.c_ulonglong, ctypes.c_longlong, ctypes.c_longlong, _VP, _VP], _I),
     "cola_linear_power": ([ctypes.POINTER(CParams), ctypes.POINTER(_D), _I, ctypes.POINTER(_D), ctypes.POINTER(_D)], _I),
     "cola_ic_2lpt": ([_VP, _VP, _VP, _VP, _VP, _VP], _I),
     "cola_deposit": ([_VP, _VP, _VP], _I),
@@ -160,6 +163,33 @@ def linear_power(p: Params, k) -> tuple[list[float], list[float]]:
     return list(pw)[:len(k)], list(tr)[:len(k)]
 
 
+def white_noise(p: Params, device=None):
+    """The library's seeded white noise of p.seed on the p.np_side^3 lattice (cola_white_noise):
+    a new float32 [n] tensor on `device` (default: the current CUDA device)."""
+    import torch
+    lib = load_library()
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    with torch.cuda.device(dev):
+        out = torch.empty((p.n,), dtype=torch.float32, device=dev)
+        cp = p.to_c()
+        _check(lib.cola_white_noise(ctypes.byref(cp), _ptr(out, torch), ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)),
+               "cola_white_noise")
+    return out
+
+
+def philox_words(seed: int, first: int, count: int, device=None):
+    """Raw Philox-4x32-10 words of counters first .. first+count-1 under `seed` (cola_philox_words):
+    a new int32 [count, 4] tensor holding the 32-bit words."""
+    import torch
+    lib = load_library()
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    with torch.cuda.device(dev):
+        out = torch.empty((count, 4), dtype=torch.int32, device=dev)
+        _check(lib.cola_philox_words(ctypes.c_ulonglong(seed), int(first), int(count), _ptr(out, torch),
+                                     ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)), "cola_philox_words")
+    return out
+
+
 def power_spectrum_noalloc(p: Params, s, nbins: int = 64, stream=None):
     """P(k) of displacements s through the allocation-free entry point (no context; meshes up to
     64^3).  Returns a new [3, nbins] float64 tensor; the library itself allocates nothing."""
@@ -229,9 +259,15 @@ class Context:
     def sync(self):
         _check(self.lib.cola_sync(self._ptr), "cola_sync")
 
+    def _noise(self, white_noise):
+        """Pointer of a caller's white noise [n], or None: the library draws the field of p.seed."""
+        if white_noise is None:
+            return None
+        return _ptr(white_noise, self.torch, (self.p.n,), self.torch.float32)
+
     # -- calls -----------------------------------------------------------------------------
-    def ic_2lpt(self, white_noise):
-        wn = _ptr(white_noise, self.torch, (self.p.n,), self.torch.float32)
+    def ic_2lpt(self, white_noise=None):
+        wn = self._noise(white_noise)
         s, v, p1, p2 = (self.empty_particles() for _ in range(4))
         _check(self.lib.cola_ic_2lpt(self._ptr, wn, self._particles(s), self._particles(v),
                                      self._particles(p1), self._particles(p2)), "cola_ic_2lpt")
@@ -297,7 +333,7 @@ class Context:
 
     def run_snapshots(self, white_noise, a_snap, nbins: int = 64, with_pk: bool = True, cic_correct: bool = False):
         """cola_run_snapshots: dict(s, v, psi1, psi2, s_snap [k,3,n], v_snap, pk_snap [k,3,nbins])."""
-        wn = _ptr(white_noise, self.torch, (self.p.n,), self.torch.float32)
+        wn = self._noise(white_noise)
         k = len(a_snap)
         s, v, p1, p2 = (self.empty_particles() for _ in range(4))
         ss = self.torch.empty((k, 3, self.p.n), dtype=self.torch.float32, device=self.device)
@@ -310,9 +346,9 @@ class Context:
                                            int(nbins), PK_CIC_CORRECT if cic_correct else 0), "cola_run_snapshots")
         return dict(s=s, v=v, psi1=p1, psi2=p2, s_snap=ss, v_snap=vs, pk_snap=pk)
 
-    def run(self, white_noise, nbins: int = 64, with_pk: bool = True, out: dict | None = None):
+    def run(self, white_noise=None, nbins: int = 64, with_pk: bool = True, out: dict | None = None):
         """A whole realisation (cola_run).  ``out`` may hold preallocated s, v, psi1, psi2, pk tensors."""
-        wn = _ptr(white_noise, self.torch, (self.p.n,), self.torch.float32)
+        wn = self._noise(white_noise)
         if out is None:
             s, v, p1, p2 = (self.empty_particles() for _ in range(4))
             pk = self.torch.empty((3, nbins), dtype=self.torch.float64, device=self.device) if with_pk else None
@@ -326,9 +362,9 @@ class Context:
         return dict(s=s, v=v, psi1=p1, psi2=p2, pk=pk)
 
     # -- reverse mode ----------------------------------------------------------------------
-    def run_checkpointed(self, white_noise):
+    def run_checkpointed(self, white_noise=None):
         """cola_run_checkpointed: returns dict(s, v, psi1, psi2, ckpt) with ckpt [nstep, 3, n]."""
-        wn = _ptr(white_noise, self.torch, (self.p.n,), self.torch.float32)
+        wn = self._noise(white_noise)
         s, v, p1, p2 = (self.empty_particles() for _ in range(4))
         ck = self.torch.empty((self.p.nstep, 3, self.p.n), dtype=self.torch.float32, device=self.device)
         _check(self.lib.cola_run_checkpointed(self._ptr, wn, self._particles(s), self._particles(v),
@@ -339,7 +375,7 @@ class Context:
     def adjoint(self, white_noise, ckpt, lam_s, lam_v=None, lam_psi1=None, lam_psi2=None):
         """cola_adjoint: dL/d(white noise) [n] from the cotangents of the final s (and optionally
         v_res, Psi1, Psi2)."""
-        wn = _ptr(white_noise, self.torch, (self.p.n,), self.torch.float32)
+        wn = self._noise(white_noise)
         ck = _ptr(ckpt, self.torch, (self.p.nstep, 3, self.p.n), self.torch.float32)
         opt = [None if t is None else self._particles(t) for t in (lam_v, lam_psi1, lam_psi2)]
         out = self.torch.empty((self.p.n,), dtype=self.torch.float32, device=self.device)
@@ -425,12 +461,13 @@ class Batch:
         ios = (BatchIO * len(params))()
         cps = (CParams * len(params))()
         for i, (p, wn) in enumerate(zip(params, white_noise)):
-            _ptr(wn, torch, (p.n,), torch.float32)
+            if wn is not None:   # None: the library draws the field of p.seed
+                _ptr(wn, torch, (p.n,), torch.float32)
             o = {k: torch.empty((3, p.n), dtype=torch.float32, device=dev) for k in ("s", "v", "psi1", "psi2")}
             o["pk"] = torch.empty((3, nbins), dtype=torch.float64, device=dev)
             o["white_noise"] = wn
             self.outputs.append(o)
-            ios[i] = BatchIO(wn.data_ptr(), o["s"].data_ptr(), o["v"].data_ptr(), o["psi1"].data_ptr(),
+            ios[i] = BatchIO(wn.data_ptr() if wn is not None else None, o["s"].data_ptr(), o["v"].data_ptr(), o["psi1"].data_ptr(),
                              o["psi2"].data_ptr(), o["pk"].data_ptr())
             cps[i] = p.to_c()
         self._ptr = ctypes.c_void_p()

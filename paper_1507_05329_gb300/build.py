@@ -18,7 +18,7 @@ BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(HERE, "libcola.so")
 SOURCES = ["fft.cu", "fft_generic.cu", "fft_fast8.cu", "fft_fast16.cu", "fft_pipe8.cu", "fft_pipe16.cu", "fft_green8.cu", "fft_green16.cu", "fft_green8e.cu", "fft_green16e.cu", "fft_rows8e.cu",
            "fft_rows16e.cu", "particles.cu", "binning.cu", "adjoint.cu", "fof.cu", "cola_batch.cu", "cola_abi.cu",
-           "cola_static.cu", "host_cosmo.cpp"]
+           "cola_static.cu", "rng.cu", "host_cosmo.cpp"]
 HEADERS = [os.path.join(CSRC, "cola_internal.h"), os.path.join(CSRC, "fft_core.cuh"), os.path.join(CSRC, "fft_fast.inc"),
            os.path.join(ROOT, "include", "cola.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -179,6 +179,16 @@ int forward3d_yx(cola_ctx* c, const Grid3& g, const FftPlan& p, float2* b) {
   return STAGED(kStFwdX, launch_pencils(p, g, 0, -1, b, c->stream));
 }
 
+// W(k) = R2C of the lattice white noise into B0: the caller's field wn, or (wn == NULL) the field
+// of params.seed drawn into B0's real rows first (the R2C then runs in place).
+int noise_spectrum(cola_ctx* c, const float* wn, float2* b0) {
+  const Grid3& g = c->lat;
+  if (wn) return STAGED(kStFwdZ, launch_r2c_rows(c->lplan, g, kSrcFloat, wn, g.n, 1.0f, b0, c->stream));
+  float* rows = reinterpret_cast<float*>(b0);
+  COLA_TRY(STAGED(kStIc, launch_white_noise(c->p.seed, c->p.np, 2LL * g.pc, rows, c->stream)));
+  return STAGED(kStFwdZ, launch_r2c_rows(c->lplan, g, kSrcFloat, rows, 2LL * g.pc, 1.0f, b0, c->stream));
+}
+
 }  // namespace
 
 extern "C" const char* cola_strerror(int status) {
@@ -223,6 +233,19 @@ extern "C" int cola_linear_power(const cola_params* params, const double* k, int
     if (transfer) transfer[i] = cosmo.transfer(k[i]);
   }
   return COLA_OK;
+}
+
+extern "C" int cola_white_noise(const cola_params* params, float* out, void* stream) {
+  if (validate(params) != COLA_OK) return COLA_ERR_INVALID;
+  COLA_TRY(check_ptr(out));
+  return launch_white_noise(params->seed, params->np, params->np, out, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int cola_philox_words(unsigned long long seed, long long first, long long count, unsigned* out,
+                                 void* stream) {
+  if (first < 0 || count < 0 || (count > 0 && check_ptr(out) != COLA_OK)) return COLA_ERR_INVALID;
+  if (count == 0) return COLA_OK;
+  return launch_philox_words(seed, first, count, out, static_cast<cudaStream_t>(stream));
 }
 
 extern "C" void cola_destroy(cola_ctx* c) {
@@ -382,7 +405,8 @@ extern "C" int cola_sync(cola_ctx* c) {
 
 extern "C" int cola_ic_2lpt(cola_ctx* c, const float* wn, float* s, float* v, float* psi1, float* psi2) {
   if (!c) return COLA_ERR_INVALID;
-  for (const void* p : {(const void*)wn, (const void*)s, (const void*)v, (const void*)psi1, (const void*)psi2})
+  if (wn) COLA_TRY(check_ptr(wn));
+  for (const void* p : {(const void*)s, (const void*)v, (const void*)psi1, (const void*)psi2})
     COLA_TRY(check_ptr(p));
   const LatticeScope scope(c);
   const Grid3& g = c->lat;
@@ -393,7 +417,7 @@ extern "C" int cola_ic_2lpt(cola_ctx* c, const float* wn, float* s, float* v, fl
   const long long n = c->pg.npart;
   const float r = (float)c->p.nmesh / (float)c->p.np;   // lattice spacings -> mesh cells
   // white noise -> W(k) -> delta_L(k) / np^3
-  COLA_TRY(STAGED(kStFwdZ, launch_r2c_rows(P, g, kSrcFloat, wn, g.n, 1.0f, B[0], c->stream)));
+  COLA_TRY(noise_spectrum(c, wn, B[0]));
   COLA_TRY(forward3d_yx(c, g, P, B[0]));
   COLA_TRY(STAGED(kStIc, launch_ic_amplitude(g, B[0], c->amp_m2, c->stream)));
   // Psi1 = i k delta_L / k^2
@@ -815,7 +839,7 @@ int lpt_adjoint(cola_ctx* c, const float* wn, float* lam_wn) {
   const float r = (float)c->p.nmesh / (float)c->p.np;
   const float inv_n3 = (float)(1.0 / ((double)g.n * g.n * g.n));
   // delta_L(k) / np^3 as in the forward
-  COLA_TRY(STAGED(kStFwdZ, launch_r2c_rows(P, g, kSrcFloat, wn, g.n, 1.0f, B[0], c->stream)));
+  COLA_TRY(noise_spectrum(c, wn, B[0]));
   COLA_TRY(forward3d_yx(c, g, P, B[0]));
   COLA_TRY(STAGED(kStIc, launch_ic_amplitude(g, B[0], c->amp_m2, c->stream)));
   // lam_S = sum_j (transpose of Psi2_j = -i kodd_j / k^2 S) lam_Psi2_j
@@ -871,7 +895,8 @@ extern "C" int cola_run_checkpointed(cola_ctx* c, const float* wn, float* s, flo
 extern "C" int cola_adjoint(cola_ctx* c, const float* wn, const float* ckpt, const float* lam_s, const float* lam_v,
                             const float* lam_psi1, const float* lam_psi2, float* lam_wn) {
   if (!c) return COLA_ERR_INVALID;
-  for (const void* p : {(const void*)wn, (const void*)ckpt, (const void*)lam_s, (const void*)lam_wn})
+  if (wn) COLA_TRY(check_ptr(wn));
+  for (const void* p : {(const void*)ckpt, (const void*)lam_s, (const void*)lam_wn})
     COLA_TRY(check_ptr(p));
   for (const void* p : {(const void*)lam_v, (const void*)lam_psi1, (const void*)lam_psi2})
     if (p) COLA_TRY(check_ptr(p));

@@ -99,8 +99,9 @@ extern "C" int cola_batch_create(const cola_params* params, const cola_batch_io*
   *out = nullptr;
   for (int i = 0; i < count; ++i) {
     const cola_batch_io& o = io[i];
-    for (const void* p : {(const void*)o.white_noise, (const void*)o.s, (const void*)o.v, (const void*)o.psi1,
-                          (const void*)o.psi2, (const void*)o.pk})
+    if ((uintptr_t)o.white_noise % 16) return COLA_ERR_INVALID;   // NULL: drawn from params[i].seed
+    for (const void* p : {(const void*)o.s, (const void*)o.v, (const void*)o.psi1, (const void*)o.psi2,
+                          (const void*)o.pk})
       if (!p || (uintptr_t)p % 16) return COLA_ERR_INVALID;
   }
   cola_batch* b = new (std::nothrow) cola_batch;

@@ -211,6 +211,11 @@ int launch_ic_to_particles(const Grid3& g, const float2* field, float scale, flo
 int launch_ic_positions(long long npart, const float* psi1, const float* psi2, float d1, float d2,
                         float* s, float* v, cudaStream_t st);
 
+// Seeded white noise (rng.cu): Philox-4x32-10 keyed by the seed, Box-Muller, one Gaussian per lattice
+// site written to out[row * row_stride + iz]; and the raw words of counters first .. first+count-1.
+int launch_white_noise(unsigned long long seed, int np, long long row_stride, float* out, cudaStream_t st);
+int launch_philox_words(unsigned long long seed, long long first, long long count, unsigned* out, cudaStream_t st);
+
 // Adjoint (adjoint.cu).
 int launch_adj_step(long long n3, const float* lam_s, float* lam_v, float* lam_p1, float* lam_p2, float* lam_f,
                     const StepScalars& sc, cudaStream_t st);

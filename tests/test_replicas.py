@@ -42,3 +42,22 @@ def test_two_replicas_on_gloo():
         assert slow == 150.0
         assert len(set(seeds)) == world
         assert rate == pytest.approx(2 * 1000 * 10 / 0.150)
+
+
+def test_bench_gpus_n_starts_n_ranks():
+    """`python bench.py --gpus 2` started by hand (no WORLD_SIZE) re-runs itself as two ranks under
+    torch.distributed.run; --launch-check makes every rank join a gloo group and report, no GPU work."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = {k: v for k, v in os.environ.items() if k not in ("WORLD_SIZE", "RANK", "LOCAL_RANK")}
+    res = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--gpus", "2", "--launch-check"],
+                         capture_output=True, text=True, timeout=300, env=env, cwd=root)
+    assert res.returncode == 0, res.stderr[-2000:]
+    lines = [json.loads(ln) for ln in res.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1, res.stdout
+    line = lines[0]
+    assert line["launch_check"] is True and line["n_gpus"] == 2
+    assert sorted(r["rank"] for r in line["ranks"]) == [0, 1]
+    assert len({r["pid"] for r in line["ranks"]}) == 2
