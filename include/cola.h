@@ -133,6 +133,17 @@ int cola_deposit(cola_ctx* ctx, const float* s, unsigned long long* rho);
  * X(k) = sum_x delta(x) exp(-i k.x)). */
 int cola_density_spectrum(cola_ctx* ctx, const float* s, float* delta_k);
 
+/* S2 and S3 on a given fixed-point density mesh, in place of the deposit (for checks of the FFT and
+ * Poisson passes on a known density, e.g. a sum of plane waves, at any mesh size).  rho: device
+ * uint64 [N][N][N], read only, interpreted as the deposit's output (delta = rho N^3 / (n 2^42) - 1,
+ * n = np^3; no total-mass check).  The passes are the context's schedule, as in cola_pm_force.
+ * cola_density_spectrum_of_mesh writes the forward spectrum as cola_density_spectrum does.
+ * cola_pm_force_of_mesh writes F_j at the m mesh cells cells[i] = (ix N + iy) N + iz (device int64
+ * [m], each in [0, N^3)) to force (device float32 [3][m]), a as in cola_pm_force. */
+int cola_density_spectrum_of_mesh(cola_ctx* ctx, const unsigned long long* rho, float* delta_k);
+int cola_pm_force_of_mesh(cola_ctx* ctx, const unsigned long long* rho, double a, const long long* cells, long long m,
+                          float* force);
+
 /* S1-S3 (+ interpolation) — PM force at the particles (§2.2 Poisson equation and eq. motion):
  * F = -grad phi with nabla^2 phi = (3/2) Om a^-1 delta, Green function -1/k^2, 4-point
  * central-difference gradient kernel, CIC interpolation with the deposit's weights.

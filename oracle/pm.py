@@ -61,3 +61,52 @@ def pm_force(s, np_side: int, nmesh: int, force_scale: float) -> np.ndarray:
     fmesh = force_mesh(density_fixed(s, np_side, nmesh), force_scale)
     cell, w1 = cic.interp_weights_fixed(s, np_side, nmesh)
     return cic.cic_interp(fmesh, cell, w1)
+
+
+# ---- closed forms for a density made of plane waves (checks at mesh sizes too big for an FFT) --------
+# delta(x) = sum_w A_w cos(2 pi m_w.x / N + phi_w) on the integer cells x, with every |m_w,i| < N/2
+# and m_w != 0.  Its DFT has (A/2) N^3 e^{+i phi} at +m and (A/2) N^3 e^{-i phi} at -m, so the force
+# of §2.2 (Green function -1/k^2, gradient kernel D, Poisson prefactor force_scale) is, per wave,
+# F_j(x) = -force_scale A D(m_j) sin(2 pi m.x / N + phi) / k^2 with k = 2 pi m / N in rad/cell.
+
+def plane_wave_density(waves, n: int, cells) -> np.ndarray:
+    """delta at flat cell indices (ix N + iy) N + iz."""
+    cells = np.asarray(cells, dtype=np.int64)
+    x = np.stack([cells // (n * n), (cells // n) % n, cells % n]).astype(np.float64)
+    out = np.zeros(cells.shape, dtype=np.float64)
+    for m, amp, phi in waves:
+        theta = 2.0 * np.pi * (m[0] * x[0] + m[1] * x[1] + m[2] * x[2]) / n + phi
+        out += amp * np.cos(theta)
+    return out
+
+
+def plane_wave_spectrum(waves, n: int) -> dict:
+    """The nonzero entries of the half spectrum [N, N, N/2+1] of the plane-wave density: {(ix, iy, iz):
+    complex value} in storage order (negative mode numbers stored at m + N; k_z in 0..N/2)."""
+    out = {}
+    for m, amp, phi in waves:
+        assert 0 < max(abs(int(c)) for c in m) and all(abs(int(c)) * 2 < n for c in m)
+        for sign in (+1, -1):
+            k = [int(sign * c) % n for c in m]
+            if k[2] > n // 2:
+                continue   # the conjugate half, not stored
+            key = tuple(k)
+            out[key] = out.get(key, 0.0) + 0.5 * amp * n ** 3 * np.exp(1j * sign * phi)
+    return out
+
+
+def plane_wave_force(waves, n: int, force_scale: float, cells) -> np.ndarray:
+    """Force [3, m] of the plane-wave density at flat cell indices, from the Green function and the
+    gradient kernel of ``green_gradient_spectra``."""
+    cells = np.asarray(cells, dtype=np.int64)
+    x = np.stack([cells // (n * n), (cells // n) % n, cells % n]).astype(np.float64)
+    out = np.zeros((3,) + cells.shape, dtype=np.float64)
+    kf = 2.0 * np.pi / n
+    for m, amp, phi in waves:
+        mm = np.asarray(m, dtype=np.int64)
+        k2 = float(np.sum(mm * mm)) * kf * kf
+        theta = 2.0 * np.pi * (mm[0] * x[0] + mm[1] * x[1] + mm[2] * x[2]) / n + phi
+        for j in range(3):
+            d = float(gradient_kernel(np.array([mm[j]]), n)[0])
+            out[j] += -force_scale * amp * d * np.sin(theta) / k2
+    return out

@@ -74,6 +74,8 @@ SIGNATURES = {
     "cola_deposit": ([_VP, _VP, _VP], _I),
     "cola_density_spectrum": ([_VP, _VP, _VP], _I),
     "cola_pm_force": ([_VP, _VP, _D, _VP], _I),
+    "cola_density_spectrum_of_mesh": ([_VP, _VP, _VP], _I),
+    "cola_pm_force_of_mesh": ([_VP, _VP, _D, _VP, ctypes.c_longlong, _VP], _I),
     "cola_step": ([_VP, _I, _VP, _VP, _VP, _VP], _I),
     "cola_run": ([_VP, _VP, _VP, _VP, _VP, _VP, _VP, _I], _I),
     "cola_power_spectrum": ([_VP, _VP, _VP, _I], _I),
@@ -285,6 +287,28 @@ class Context:
         _check(self.lib.cola_density_spectrum(self._ptr, self._particles(s), _ptr(dk, self.torch)),
                "cola_density_spectrum")
         return dk
+
+    def density_spectrum_of_mesh(self, rho):
+        """cola_density_spectrum_of_mesh: forward spectrum [N, N, N/2+1, 2] of a given fixed-point mesh."""
+        n = self.p.nmesh
+        _ptr(rho, self.torch, (n, n, n), self.torch.int64)
+        dk = self.torch.empty((n, n, n // 2 + 1, 2), dtype=self.torch.float32, device=self.device)
+        _check(self.lib.cola_density_spectrum_of_mesh(self._ptr, _ptr(rho, self.torch), _ptr(dk, self.torch)),
+               "cola_density_spectrum_of_mesh")
+        return dk
+
+    def pm_force_of_mesh(self, rho, a: float, cells):
+        """cola_pm_force_of_mesh: the force components [3, m] at mesh cells (int64 flat indices)."""
+        n = self.p.nmesh
+        _ptr(rho, self.torch, (n, n, n), self.torch.int64)
+        m = int(cells.numel())
+        if m and (int(cells.min()) < 0 or int(cells.max()) >= n ** 3):
+            raise ValueError("cells must lie in [0, N^3)")
+        out = self.torch.empty((3, m), dtype=self.torch.float32, device=self.device)
+        _check(self.lib.cola_pm_force_of_mesh(self._ptr, _ptr(rho, self.torch), float(a),
+                                              _ptr(cells, self.torch, (m,), self.torch.int64), m, _ptr(out, self.torch)),
+               "cola_pm_force_of_mesh")
+        return out
 
     def pm_force(self, s, a: float):
         f = self.empty_particles()

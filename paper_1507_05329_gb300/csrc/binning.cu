@@ -22,11 +22,15 @@
 #include "cola_internal.h"
 
 #include <cstdio>
+#include <type_traits>
 
 namespace cola {
 namespace {
 
 constexpr int kThreads = 256;
+#ifndef COLA_DEPOSIT_MIN_BLOCKS
+#define COLA_DEPOSIT_MIN_BLOCKS 6   // resident deposit CTAs per SM the register budget is sized for
+#endif
 
 int check_launch(const char* what) {
   const cudaError_t e = cudaGetLastError();
@@ -75,9 +79,12 @@ __device__ __forceinline__ unsigned agg_inc(unsigned* counter, int key, bool wan
 
 // Bin keys of one particle: primary tile and up to seven spill tiles (-1 = none).  Tile index
 // (bx * nt + by) * nz + bz runs fastest along z.
+// LT, LZ: compile-time log2 of the tile sides (the common 8 x 8 x 32 tiles), or 0 to read them from b.
+template <int LT, int LZ>
 __device__ __forceinline__ void tile_keys(const BinGeom& b, int cx, int cy, int cz, int* k) {
-  const int bx = cx >> b.lt, by = cy >> b.lt, bz = cz >> b.lz;
-  const int m = (1 << b.lt) - 1, mz = (1 << b.lz) - 1;
+  const int lt = LT ? LT : b.lt, lz = LZ ? LZ : b.lz;
+  const int bx = cx >> lt, by = cy >> lt, bz = cz >> lz;
+  const int m = (1 << lt) - 1, mz = (1 << lz) - 1;
   // with a single tile along an axis the cloud wraps inside the tile itself: no spill there
   const bool sx = b.nt > 1 && (cx & m) == m, sy = b.nt > 1 && (cy & m) == m, sz = b.nz > 1 && (cz & mz) == mz;
   const int bxs[2] = {bx, bx + 1 == b.nt ? 0 : bx + 1};
@@ -91,11 +98,10 @@ __device__ __forceinline__ void tile_keys(const BinGeom& b, int cx, int cy, int 
   }
 }
 
-template <bool SCATTER>
-__global__ void __launch_bounds__(kThreads) k_bin(ParticleGeom pg, BinGeom b, const float* __restrict__ s,
+template <bool SCATTER, int LT, int LZ, bool F32>
+__global__ void __launch_bounds__(kThreads) k_bin(ParticleGeom pg, BinGeom b, FixedGeo fg, const float* __restrict__ s,
                                                   unsigned* cnt_p, unsigned* cnt_s, unsigned* ent_p, unsigned* ent_s) {
   const long long n = pg.npart;
-  const long long modulus = (long long)pg.n << kFracBits;
   const int np = pg.np;
   const long long nrows = (long long)np * np;
   // the block walks (row, chunk) pairs; the positions of the next pair are loaded before this
@@ -129,10 +135,11 @@ __global__ void __launch_bounds__(kThreads) k_bin(ParticleGeom pg, BinGeom b, co
     const bool live = qz < np;
     int k[8] = {-1, -1, -1, -1, -1, -1, -1, -1};
     if (live) {
-      const int cx = (int)(fixed_coord(qx, p0, pg.r_fixed, modulus) >> kFracBits);
-      const int cy = (int)(fixed_coord(qy, p1, pg.r_fixed, modulus) >> kFracBits);
-      const int cz = (int)(fixed_coord(qz, p2, pg.r_fixed, modulus) >> kFracBits);
-      tile_keys(b, cx, cy, cz, k);
+      int cx, cy, cz, f;
+      cell_frac<F32>(qx, p0, fg, &cx, &f);
+      cell_frac<F32>(qy, p1, fg, &cy, &f);
+      cell_frac<F32>(qz, p2, fg, &cz, &f);
+      tile_keys<LT, LZ>(b, cx, cy, cz, k);
     }
     const unsigned packed = pack_q(qx, qy, qz);
     if (__any_sync(__activemask(), live)) {
@@ -244,67 +251,67 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const unsigned* __r
   }
 }
 
-// Tile-wise deposit: shared accumulator [T][T][TZ] of 64-bit fixed-point sums.
-__global__ void __launch_bounds__(kThreads) k_deposit_tiles(ParticleGeom pg, BinGeom b, const float* __restrict__ s,
+// Tile-wise deposit: shared accumulator [T][T][TZ] of 64-bit fixed-point sums.  The tile's primary
+// and spill entries form one index range, so a CTA's threads run out of work together.
+template <int LT, int LZ, bool F32>
+__global__ void __launch_bounds__(kThreads, COLA_DEPOSIT_MIN_BLOCKS) k_deposit_tiles(ParticleGeom pg, BinGeom b, FixedGeo fg,
+                                                           const float* __restrict__ s,
                                                            const unsigned* __restrict__ off_p,
                                                            const unsigned* __restrict__ ent_p,
                                                            const unsigned* __restrict__ off_s,
                                                            const unsigned* __restrict__ ent_s,
                                                            unsigned long long* rho) {
   extern __shared__ unsigned long long acc[];
-  const int nm = pg.n, T = 1 << b.lt, TZ = 1 << b.lz;
+  const int lt = LT ? LT : b.lt, lz = LZ ? LZ : b.lz;
+  const int nm = pg.n, T = 1 << lt, TZ = 1 << lz;
   const int tile = blockIdx.x;
   const int bz = tile % b.nz, bxy = tile / b.nz;
   const int bx = bxy / b.nt, by = bxy - bx * b.nt;
-  const int x0 = bx << b.lt, y0 = by << b.lt, z0 = bz << b.lz;
-  const int cells = (T * T) << b.lz;
+  const int x0 = bx << lt, y0 = by << lt, z0 = bz << lz;
+  const int cells = (T * T) << lz;
   for (int i = threadIdx.x; i < cells; i += blockDim.x) acc[i] = 0ULL;
   __syncthreads();
   const long long n = pg.npart;
-  const long long modulus = (long long)nm << kFracBits;
-  for (int list = 0; list < 2; ++list) {
-    const unsigned* off = list ? off_s : off_p;
-    const unsigned* ent = list ? ent_s : ent_p;
-    const unsigned e0 = off[tile], e1 = off[tile + 1];
-    for (unsigned e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-      int q[3];
-      long long id;
-      unpack_q(ent[e], pg.np, q, &id);
-      int c[3];
-      unsigned long long w1[3], w0[3];
+  const unsigned p0 = off_p[tile], np_t = off_p[tile + 1] - p0;
+  const unsigned s0 = off_s[tile], total = np_t + (off_s[tile + 1] - s0);
+  for (unsigned k = threadIdx.x; k < total; k += blockDim.x) {
+    int q[3];
+    long long id;
+    unpack_q(k < np_t ? ent_p[p0 + k] : ent_s[s0 + (k - np_t)], pg.np, q, &id);
+    int c[3];
+    unsigned w1[3], w0[3];
 #pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        const long long g = fixed_coord(q[a], __ldg(s + a * n + id), pg.r_fixed, modulus);
-        c[a] = (int)(g >> kFracBits);
-        w1[a] = (unsigned long long)((g >> (kFracBits - 14)) & (kWeightOne - 1));
-        w0[a] = kWeightOne - w1[a];
-      }
-      int lz[2];
+    for (int a = 0; a < 3; ++a) {
+      int f;
+      cell_frac<F32>(q[a], __ldg(s + a * n + id), fg, &c[a], &f);
+      w1[a] = (unsigned)f;
+      w0[a] = kWeightOne - w1[a];
+    }
+    int lz2[2];
 #pragma unroll
-      for (int dz = 0; dz < 2; ++dz) {
-        int iz = c[2] + dz;
-        if (iz == nm) iz = 0;
-        lz[dz] = iz - z0;
-      }
+    for (int dz = 0; dz < 2; ++dz) {
+      int iz = c[2] + dz;
+      if (iz == nm) iz = 0;
+      lz2[dz] = iz - z0;
+    }
 #pragma unroll
-      for (int dx = 0; dx < 2; ++dx) {
-        int ix = c[0] + dx;
-        if (ix == nm) ix = 0;
-        const int lx = ix - x0;
-        if (lx < 0 || lx >= T) continue;
+    for (int dx = 0; dx < 2; ++dx) {
+      int ix = c[0] + dx;
+      if (ix == nm) ix = 0;
+      const int lx = ix - x0;
+      if (lx < 0 || lx >= T) continue;
 #pragma unroll
-        for (int dy = 0; dy < 2; ++dy) {
-          int iy = c[1] + dy;
-          if (iy == nm) iy = 0;
-          const int ly = iy - y0;
-          if (ly < 0 || ly >= T) continue;
-          const unsigned long long wxy = (dx ? w1[0] : w0[0]) * (dy ? w1[1] : w0[1]);
-          unsigned long long* col = acc + ((lx * T + ly) << b.lz);
+      for (int dy = 0; dy < 2; ++dy) {
+        int iy = c[1] + dy;
+        if (iy == nm) iy = 0;
+        const int ly = iy - y0;
+        if (ly < 0 || ly >= T) continue;
+        const unsigned wxy = (dx ? w1[0] : w0[0]) * (dy ? w1[1] : w0[1]);   // <= 2^28
+        unsigned long long* col = acc + ((lx * T + ly) << lz);
 #pragma unroll
-          for (int dz = 0; dz < 2; ++dz) {
-            const unsigned long long w = wxy * (dz ? w1[2] : w0[2]);
-            if (w && lz[dz] >= 0 && lz[dz] < TZ) smem_add64(col + lz[dz], w);
-          }
+        for (int dz = 0; dz < 2; ++dz) {
+          const unsigned long long w = (unsigned long long)wxy * (dz ? w1[2] : w0[2]);   // <= 2^42
+          if (w && lz2[dz] >= 0 && lz2[dz] < TZ) smem_add64(col + lz2[dz], w);
         }
       }
     }
@@ -312,8 +319,8 @@ __global__ void __launch_bounds__(kThreads) k_deposit_tiles(ParticleGeom pg, Bin
   __syncthreads();
   // the tile owns its cells: plain, coalesced stores of T*T column segments of TZ cells
   for (int i = threadIdx.x; i < cells; i += blockDim.x) {
-    const int col = i >> b.lz, z = i & (TZ - 1);
-    const int lx = col >> b.lt, ly = col & (T - 1);
+    const int col = i >> lz, z = i & (TZ - 1);
+    const int lx = col >> lt, ly = col & (T - 1);
     rho[((long long)(x0 + lx) * nm + (y0 + ly)) * nm + z0 + z] = acc[i];
   }
 }
@@ -330,6 +337,11 @@ __host__ __device__ __forceinline__ int gather_floats(const BinGeom& b) {
   const int hx = (1 << b.lt) + 1, hp = ((1 << b.lz) + 1 + 3) & ~3;
   return 3 * hx * hx * hp;
 }
+template <int LT, int LZ>
+__device__ __forceinline__ int gather_floats_t(const BinGeom& b) {
+  const int hx = (1 << (LT ? LT : b.lt)) + 1, hp = ((1 << (LZ ? LZ : b.lz)) + 1 + 3) & ~3;
+  return 3 * hx * hx * hp;
+}
 
 __device__ __forceinline__ GatherTile gather_tile_origin(const BinGeom& b, int tile) {
   const int bz = tile % b.nz, bxy = tile / b.nz;
@@ -340,10 +352,11 @@ __device__ __forceinline__ GatherTile gather_tile_origin(const BinGeom& b, int t
 // Issue (and commit as one group) the asynchronous copies of a tile's forces into fsm: TZ/4
 // chunks of 16 bytes per row (rows start 16-byte aligned: z0 is a multiple of TZ and real rows
 // hold 2 pc floats, pc even) plus the 4-byte periodic halo cell.
+template <int LT, int LZ>
 __device__ __forceinline__ void gather_stage(float* fsm, const BinGeom& b, int nm, const GatherTile& t,
                                              const float* __restrict__ f0, const float* __restrict__ f1,
                                              const float* __restrict__ f2, long long rs) {
-  const int hx = (1 << b.lt) + 1, zl = 1 << b.lz, hp = (zl + 1 + 3) & ~3;
+  const int hx = (1 << (LT ? LT : b.lt)) + 1, zl = 1 << (LZ ? LZ : b.lz), hp = (zl + 1 + 3) & ~3;
   const int rows = 3 * hx * hx, chunks = (zl >> 2) + 1;
   for (int op = threadIdx.x; op < rows * chunks; op += blockDim.x) {
     const int r = op / chunks, ch = op - r * chunks;
@@ -369,17 +382,16 @@ __device__ __forceinline__ void gather_stage(float* fsm, const BinGeom& b, int n
 
 // Interpolate the staged forces at the tile's particles e0..e1 (and kick and drift).  Returns
 // whether a non-finite state was written.
-template <bool KICK>
+template <bool KICK, int LT, int LZ, bool F32>
 __device__ __forceinline__ bool gather_particles(const float* fsm, const ParticleGeom& pg, const BinGeom& b,
-                                                 const GatherTile& t, unsigned e0, unsigned e1,
+                                                 const FixedGeo& fg, const GatherTile& t, unsigned e0, unsigned e1,
                                                  const unsigned* __restrict__ ent_p, const unsigned* ent_s,
                                                  unsigned ne, const float* __restrict__ s_in,
                                                  float* __restrict__ force_out, float* s, float* v,
                                                  const float* __restrict__ psi1, const float* __restrict__ psi2,
                                                  const KickDrift& kd) {
-  const int hx = (1 << b.lt) + 1, hp = ((1 << b.lz) + 1 + 3) & ~3;
+  const int hx = (1 << (LT ? LT : b.lt)) + 1, hp = ((1 << (LZ ? LZ : b.lz)) + 1 + 3) & ~3;
   const long long n = pg.npart;
-  const long long modulus = (long long)pg.n << kFracBits;
   const float inv_one = 1.0f / kWeightOne;
   bool bad = false;
   const float* sp = KICK ? s : s_in;
@@ -413,9 +425,9 @@ __device__ __forceinline__ bool gather_particles(const float* fsm, const Particl
     float w1[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      const long long g = fixed_coord(q[a], sv[a], pg.r_fixed, modulus);
-      c[a] = (int)(g >> kFracBits);
-      w1[a] = (float)((int)(g >> (kFracBits - 14)) & (kWeightOne - 1)) * inv_one;
+      int f;
+      cell_frac<F32>(q[a], sv[a], fg, &c[a], &f);
+      w1[a] = (float)f * inv_one;
     }
     const int lx = c[0] - t.x0, ly = c[1] - t.y0, lz = c[2] - t.z0;   // base cell inside the tile
     float fr[3] = {0.f, 0.f, 0.f};
@@ -454,8 +466,8 @@ __device__ __forceinline__ bool gather_particles(const float* fsm, const Particl
 }
 
 // One CTA per tile.
-template <bool KICK>
-__global__ void __launch_bounds__(kThreads) k_gather_tiles(ParticleGeom pg, BinGeom b,
+template <bool KICK, int LT, int LZ, bool F32>
+__global__ void __launch_bounds__(kThreads) k_gather_tiles(ParticleGeom pg, BinGeom b, FixedGeo fg,
                                                           const unsigned* __restrict__ off_p,
                                                           const unsigned* __restrict__ ent_p,
                                                           const float* __restrict__ f0, const float* __restrict__ f1,
@@ -469,24 +481,24 @@ __global__ void __launch_bounds__(kThreads) k_gather_tiles(ParticleGeom pg, BinG
   if (e0 == e1) return;                          // empty (uniform across the block)
   const GatherTile t = gather_tile_origin(b, tile);
   // the tile's first kGatherEnt entries travel with the forces: one dependent global load fewer
-  unsigned* ent_s = reinterpret_cast<unsigned*>(fsm + gather_floats(b));
+  unsigned* ent_s = reinterpret_cast<unsigned*>(fsm + gather_floats_t<LT, LZ>(b));
   const unsigned ne = e1 - e0 < (unsigned)kGatherEnt ? e1 - e0 : (unsigned)kGatherEnt;
   for (unsigned i = threadIdx.x; i < ne; i += blockDim.x) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(ent_s + i);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(ent_p + e0 + i) : "memory");
   }
-  gather_stage(fsm, b, pg.n, t, f0, f1, f2, rs);
+  gather_stage<LT, LZ>(fsm, b, pg.n, t, f0, f1, f2, rs);
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
   __syncthreads();
-  const bool bad = gather_particles<KICK>(fsm, pg, b, t, e0, e1, ent_p, ent_s, ne, s_in, force_out, s, v, psi1, psi2,
-                                          kd);
+  const bool bad = gather_particles<KICK, LT, LZ, F32>(fsm, pg, b, fg, t, e0, e1, ent_p, ent_s, ne, s_in, force_out,
+                                                       s, v, psi1, psi2, kd);
   if (KICK && __syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flags, 2);
 }
 
 // Persistent variant: each CTA walks tiles t = blockIdx.x + i gridDim.x with two staging buffers;
 // the next non-empty tile's forces are copied (cp.async) while the current tile's particles run.
-template <bool KICK>
-__global__ void __launch_bounds__(kThreads) k_gather_tiles_pipe(ParticleGeom pg, BinGeom b,
+template <bool KICK, int LT, int LZ, bool F32>
+__global__ void __launch_bounds__(kThreads) k_gather_tiles_pipe(ParticleGeom pg, BinGeom b, FixedGeo fg,
                                                                const unsigned* __restrict__ off_p,
                                                                const unsigned* __restrict__ ent_p,
                                                                const float* __restrict__ f0,
@@ -509,14 +521,15 @@ __global__ void __launch_bounds__(kThreads) k_gather_tiles_pipe(ParticleGeom pg,
   };
   int t = next_tile(blockIdx.x);
   if (t >= ntiles) return;
-  gather_stage(bcur, b, pg.n, gather_tile_origin(b, t), f0, f1, f2, rs);
+  gather_stage<LT, LZ>(bcur, b, pg.n, gather_tile_origin(b, t), f0, f1, f2, rs);
   bool bad = false;
   while (t < ntiles) {
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     __syncthreads();   // tile t staged; every thread is done with the other buffer
     const int tn = next_tile(t + gridDim.x);
-    if (tn < ntiles) gather_stage(bnext, b, pg.n, gather_tile_origin(b, tn), f0, f1, f2, rs);
-    bad |= gather_particles<KICK>(bcur, pg, b, gather_tile_origin(b, t), off_p[t], off_p[t + 1], ent_p, nullptr, 0u,
+    if (tn < ntiles) gather_stage<LT, LZ>(bnext, b, pg.n, gather_tile_origin(b, tn), f0, f1, f2, rs);
+    bad |= gather_particles<KICK, LT, LZ, F32>(bcur, pg, b, fg, gather_tile_origin(b, t), off_p[t], off_p[t + 1], ent_p,
+                                               nullptr, 0u,
                                   s_in, force_out, s, v, psi1, psi2, kd);
     float* tmp = bcur;
     bcur = bnext;
@@ -578,21 +591,41 @@ int launch_excl_scan(const unsigned* cnt, int m, unsigned* seg, unsigned* off, u
   return check_launch("excl_scan");
 }
 
+namespace {
+template <int V>
+using IntC = std::integral_constant<int, V>;
+
+// Calls go(LT, LZ, F32) with the compile-time instance that matches the geometry: the common
+// 8 x 8 x 32 tiles or run-time tile sides, and the 32-bit fixed-point path below 2048 cells.
+template <class Go>
+void with_instance(const BinGeom& b, int nmesh, Go&& go) {
+  const bool common = b.lt == 3 && b.lz == 5;
+  const bool f32 = nmesh < 2048;
+  if (common && f32) go(IntC<3>{}, IntC<5>{}, std::true_type{});
+  else if (common) go(IntC<3>{}, IntC<5>{}, std::false_type{});
+  else if (f32) go(IntC<0>{}, IntC<0>{}, std::true_type{});
+  else go(IntC<0>{}, IntC<0>{}, std::false_type{});
+}
+
+template <class K>
+void smem_limit(K kernel, int bytes) {
+  if (first_use_on_device(reinterpret_cast<const void*>(kernel)))
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+}  // namespace
+
 int launch_binning(const ParticleGeom& pg, const BinGeom& b, const float* s, BinBuffers& bb, cudaStream_t st) {
-  if (first_use_on_device(reinterpret_cast<const void*>(&launch_binning))) {
-    cudaFuncSetAttribute(k_deposit_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
-    cudaFuncSetAttribute(k_gather_tiles<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
-    cudaFuncSetAttribute(k_gather_tiles<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
-    cudaFuncSetAttribute(k_gather_tiles_pipe<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024);
-    cudaFuncSetAttribute(k_gather_tiles_pipe<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024);
-  }
   const long long rows = (long long)pg.np * pg.np;
   const unsigned grid = (unsigned)(rows < 152LL * 64 ? rows : 152LL * 64);
   const int th = pg.np < kThreads ? ((pg.np + 31) / 32) * 32 : kThreads;
+  const FixedGeo fg = fixed_geo(pg.n, pg.r_fixed);
   if (cudaMemsetAsync(bb.cnt_p, 0, (size_t)b.tiles * sizeof(unsigned), st) != cudaSuccess ||
       cudaMemsetAsync(bb.cnt_s, 0, (size_t)b.tiles * sizeof(unsigned), st) != cudaSuccess)
     return COLA_ERR_CUDA;
-  k_bin<false><<<grid, th, 0, st>>>(pg, b, s, bb.cnt_p, bb.cnt_s, nullptr, nullptr);
+  with_instance(b, pg.n, [&](auto lt, auto lz, auto f32) {
+    k_bin<false, decltype(lt)::value, decltype(lz)::value, decltype(f32)::value>
+        <<<grid, th, 0, st>>>(pg, b, fg, s, bb.cnt_p, bb.cnt_s, nullptr, nullptr);
+  });
   int e = check_launch("bin_count");
   if (e != COLA_OK) return e;
   const int nseg = (b.tiles + kScanSeg - 1) / kScanSeg;
@@ -601,14 +634,21 @@ int launch_binning(const ParticleGeom& pg, const BinGeom& b, const float* s, Bin
   k_scan_apply<<<dim3(nseg, 2), kScanThreads, 0, st>>>(bb.cnt_p, bb.cnt_s, b.tiles, bb.seg, bb.off_p, bb.off_s,
                                                        bb.cur_p, bb.cur_s);
   if ((e = check_launch("bin_scan")) != COLA_OK) return e;
-  k_bin<true><<<grid, th, 0, st>>>(pg, b, s, bb.cur_p, bb.cur_s, bb.ent_p, bb.ent_s);
+  with_instance(b, pg.n, [&](auto lt, auto lz, auto f32) {
+    k_bin<true, decltype(lt)::value, decltype(lz)::value, decltype(f32)::value>
+        <<<grid, th, 0, st>>>(pg, b, fg, s, bb.cur_p, bb.cur_s, bb.ent_p, bb.ent_s);
+  });
   return check_launch("bin_scatter");
 }
 
 int launch_deposit_tiles(const ParticleGeom& pg, const BinGeom& b, const float* s, const BinBuffers& bb,
                          unsigned long long* rho, cudaStream_t st) {
-  k_deposit_tiles<<<b.tiles, kThreads, bin_smem_bytes(b, pg.n), st>>>(pg, b, s, bb.off_p, bb.ent_p, bb.off_s, bb.ent_s,
-                                                                  rho);
+  const FixedGeo fg = fixed_geo(pg.n, pg.r_fixed);
+  with_instance(b, pg.n, [&](auto lt, auto lz, auto f32) {
+    auto k = k_deposit_tiles<decltype(lt)::value, decltype(lz)::value, decltype(f32)::value>;
+    smem_limit(k, 64 * 1024);
+    k<<<b.tiles, kThreads, bin_smem_bytes(b, pg.n), st>>>(pg, b, fg, s, bb.off_p, bb.ent_p, bb.off_s, bb.ent_s, rho);
+  });
   return check_launch("deposit_tiles");
 }
 
@@ -618,6 +658,7 @@ int launch_gather_tiles(const ParticleGeom& pg, const BinGeom& b, const BinBuffe
   const size_t sm = gather_smem_bytes(b);
   const size_t sm_ent = (size_t)gather_floats(b) * sizeof(float) + kGatherEnt * sizeof(unsigned);
   const KickDrift k = kd ? *kd : KickDrift{};
+  const FixedGeo fg = fixed_geo(pg.n, pg.r_fixed);
   if (pipelined) {
     // two staging buffers per CTA: as many CTAs per SM as the shared memory holds (at most 4)
     int dev = 0, sms = 152;
@@ -626,21 +667,38 @@ int launch_gather_tiles(const ParticleGeom& pg, const BinGeom& b, const BinBuffe
     if (per_sm > 4) per_sm = 4;
     if (per_sm < 1) per_sm = 1;
     const int ctas = b.tiles < sms * per_sm ? b.tiles : sms * per_sm;
-    if (kd)
-      k_gather_tiles_pipe<true><<<ctas, kThreads, 2 * sm, st>>>(pg, b, bb.off_p, bb.ent_p, f[0], f[1], f[2], rs,
-                                                                 nullptr, nullptr, s, v, psi1, psi2, k, flags);
-    else
-      k_gather_tiles_pipe<false><<<ctas, kThreads, 2 * sm, st>>>(pg, b, bb.off_p, bb.ent_p, f[0], f[1], f[2], rs, s_in,
-                                                                  force_out, nullptr, nullptr, nullptr, nullptr, k,
-                                                                  flags);
+    with_instance(b, pg.n, [&](auto lt, auto lz, auto f32) {
+      constexpr int LT = decltype(lt)::value, LZ = decltype(lz)::value;
+      constexpr bool F32 = decltype(f32)::value;
+      if (kd) {
+        auto kern = k_gather_tiles_pipe<true, LT, LZ, F32>;
+        smem_limit(kern, 128 * 1024);
+        kern<<<ctas, kThreads, 2 * sm, st>>>(pg, b, fg, bb.off_p, bb.ent_p, f[0], f[1], f[2], rs, nullptr, nullptr, s,
+                                             v, psi1, psi2, k, flags);
+      } else {
+        auto kern = k_gather_tiles_pipe<false, LT, LZ, F32>;
+        smem_limit(kern, 128 * 1024);
+        kern<<<ctas, kThreads, 2 * sm, st>>>(pg, b, fg, bb.off_p, bb.ent_p, f[0], f[1], f[2], rs, s_in, force_out,
+                                             nullptr, nullptr, nullptr, nullptr, k, flags);
+      }
+    });
     return check_launch("gather_tiles_pipe");
   }
-  if (kd)
-    k_gather_tiles<true><<<b.tiles, kThreads, sm_ent, st>>>(pg, b, bb.off_p, bb.ent_p, f[0], f[1], f[2], rs, nullptr,
-                                                             nullptr, s, v, psi1, psi2, k, flags);
-  else
-    k_gather_tiles<false><<<b.tiles, kThreads, sm_ent, st>>>(pg, b, bb.off_p, bb.ent_p, f[0], f[1], f[2], rs, s_in,
-                                                              force_out, nullptr, nullptr, nullptr, nullptr, k, flags);
+  with_instance(b, pg.n, [&](auto lt, auto lz, auto f32) {
+    constexpr int LT = decltype(lt)::value, LZ = decltype(lz)::value;
+    constexpr bool F32 = decltype(f32)::value;
+    if (kd) {
+      auto kern = k_gather_tiles<true, LT, LZ, F32>;
+      smem_limit(kern, 64 * 1024);
+      kern<<<b.tiles, kThreads, sm_ent, st>>>(pg, b, fg, bb.off_p, bb.ent_p, f[0], f[1], f[2], rs, nullptr, nullptr, s,
+                                              v, psi1, psi2, k, flags);
+    } else {
+      auto kern = k_gather_tiles<false, LT, LZ, F32>;
+      smem_limit(kern, 64 * 1024);
+      kern<<<b.tiles, kThreads, sm_ent, st>>>(pg, b, fg, bb.off_p, bb.ent_p, f[0], f[1], f[2], rs, s_in, force_out,
+                                              nullptr, nullptr, nullptr, nullptr, k, flags);
+    }
+  });
   return check_launch("gather_tiles");
 }
 

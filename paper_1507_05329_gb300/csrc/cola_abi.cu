@@ -143,22 +143,27 @@ int gather(cola_ctx* c, const float* s_in, float* force, float* s, float* v, con
                                          c->stream));
 }
 
-int deposit_and_forward_yz(cola_ctx* c, const float* s) {
+// S2 (z, y) of a fixed-point mesh into cbuf[2]; with check_mass, the exact total-mass (overflow)
+// check of the deposit rides along the z pass.
+int forward_yz(cola_ctx* c, const unsigned long long* rho, bool check_mass) {
   const Grid3& g = c->mesh;
   const size_t n3 = (size_t)g.n * g.n * g.n;
-  COLA_TRY(deposit_mesh(c, s, c->rho));
   const float scale = (float)((double)n3 / ((double)c->pg.npart * 4398046511104.0));   // N^3 / (n 2^42)
-  COLA_TRY(STAGED(kStFwdZ, launch_r2c_rows(c->mplan, g, kSrcFixedPoint, c->rho, g.n, scale, c->cbuf[2], c->stream,
-                                           c->mass_acc)));
-  COLA_TRY(launch_mass_check(c->pg, nullptr, false, c->mass_acc, c->flags, c->stream));
+  COLA_TRY(STAGED(kStFwdZ, launch_r2c_rows(c->mplan, g, kSrcFixedPoint, rho, g.n, scale, c->cbuf[2], c->stream,
+                                           check_mass ? c->mass_acc : nullptr)));
+  if (check_mass) COLA_TRY(launch_mass_check(c->pg, nullptr, false, c->mass_acc, c->flags, c->stream));
   COLA_TRY(STAGED(kStFwdY, launch_pencils(c->mplan, g, 1, -1, c->cbuf[2], c->stream)));
   return COLA_OK;
 }
 
-// S1-S3: the three force components as real fields in cbuf[0..2] (rows of 2 pc floats).
-int force_mesh(cola_ctx* c, const float* s, double force_scale) {
+int deposit_and_forward_yz(cola_ctx* c, const float* s) {
+  COLA_TRY(deposit_mesh(c, s, c->rho));
+  return forward_yz(c, c->rho, true);
+}
+
+// S3 after forward_yz: the three force components as real fields in cbuf[0..2] (rows of 2 pc floats).
+int green_and_inverse(cola_ctx* c, double force_scale) {
   const Grid3& g = c->mesh;
-  COLA_TRY(deposit_and_forward_yz(c, s));
   float2* const outs[3] = {c->cbuf[0], c->cbuf[1], c->cbuf[2]};
   COLA_TRY(STAGED(kStGreenX, launch_green_x(c->mplan, g, c->cbuf[2], outs, c->dtab, (float)force_scale, c->stream)));
   for (int j = 0; j < 3; ++j) {
@@ -166,6 +171,12 @@ int force_mesh(cola_ctx* c, const float* s, double force_scale) {
     COLA_TRY(STAGED(kStInvZ, launch_c2r_rows(c->mplan, g, c->cbuf[j], c->stream)));
   }
   return COLA_OK;
+}
+
+// S1-S3: the three force components as real fields in cbuf[0..2] (rows of 2 pc floats).
+int force_mesh(cola_ctx* c, const float* s, double force_scale) {
+  COLA_TRY(deposit_and_forward_yz(c, s));
+  return green_and_inverse(c, force_scale);
 }
 
 int inverse3d(cola_ctx* c, const Grid3& g, const FftPlan& p, float2* b) {
@@ -464,6 +475,30 @@ extern "C" int cola_density_spectrum(cola_ctx* c, const float* s, float* delta_k
   COLA_TRY(deposit_and_forward_yz(c, s));
   COLA_TRY(STAGED(kStFwdX, launch_pencils(c->mplan, c->mesh, 0, -1, c->cbuf[2], c->stream)));
   return launch_dense_spectrum(c->mesh, c->cbuf[2], delta_k, c->stream);
+}
+
+extern "C" int cola_density_spectrum_of_mesh(cola_ctx* c, const unsigned long long* rho, float* delta_k) {
+  if (!c) return COLA_ERR_INVALID;
+  COLA_TRY(check_ptr(rho));
+  COLA_TRY(check_ptr(delta_k));
+  COLA_TRY(forward_yz(c, rho, false));
+  COLA_TRY(STAGED(kStFwdX, launch_pencils(c->mplan, c->mesh, 0, -1, c->cbuf[2], c->stream)));
+  return launch_dense_spectrum(c->mesh, c->cbuf[2], delta_k, c->stream);
+}
+
+extern "C" int cola_pm_force_of_mesh(cola_ctx* c, const unsigned long long* rho, double a, const long long* cells,
+                                     long long m, float* force) {
+  if (!c || !(a > 0.0) || m < 0) return COLA_ERR_INVALID;
+  COLA_TRY(check_ptr(rho));
+  if (m > 0) {
+    COLA_TRY(check_ptr(cells));
+    COLA_TRY(check_ptr(force));
+  }
+  COLA_TRY(forward_yz(c, rho, false));
+  COLA_TRY(green_and_inverse(c, 1.5 * c->p.omega_m / a));
+  const float* f[3] = {reinterpret_cast<float*>(c->cbuf[0]), reinterpret_cast<float*>(c->cbuf[1]),
+                       reinterpret_cast<float*>(c->cbuf[2])};
+  return launch_sample_mesh(c->mesh, f, cells, m, force, c->stream);
 }
 
 extern "C" int cola_pm_force(cola_ctx* c, const float* s, double a, float* force) {

@@ -147,6 +147,43 @@ __device__ __forceinline__ long long fixed_coord(int q, float s, long long r_fix
   }
   return g;
 }
+
+// The same G with 32-bit integer arithmetic where that is exact, else fixed_coord.  |s| < lim cells
+// with lim = min(N, 2047 - N) keeps q R + rint(s 2^20) inside (-N 2^20, 2047 2^20) (no int32
+// overflow) and one conditional add or subtract from [0, N 2^20); s 2^20 is exact in FP32 (a power of
+// two scaling) and fits an int32, so its round-to-nearest-even is the one fixed_coord takes.  NaN and
+// infinite s fail the test and take fixed_coord: the result is bit-identical for every input.
+struct FixedGeo {
+  long long r_fixed, modulus;
+  float lim;   // 0 when N >= 1024 + 1023 (no 32-bit fast path)
+};
+__host__ __device__ __forceinline__ FixedGeo fixed_geo(int nmesh, long long r_fixed) {
+  const int room = 2047 - nmesh;
+  const int lim = room < nmesh ? room : nmesh;
+  return FixedGeo{r_fixed, (long long)nmesh << kFracBits, lim > 0 ? (float)lim : 0.0f};
+}
+// Cell G >> 20 and 14-bit weight fraction (G >> 6) & (2^14 - 1) of one axis.  F32 (meshes below
+// 2048 cells, where every G fits an int) takes the 32-bit path when |s| < lim.
+template <bool F32>
+__device__ __forceinline__ void cell_frac(int q, float s, const FixedGeo& f, int* cell, int* frac) {
+  if (F32) {
+    int g;
+    if (fabsf(s) < f.lim) {
+      const int m = (int)f.modulus;
+      g = q * (int)f.r_fixed + __float2int_rn(s * (float)kFracOne);
+      if (g < 0) g += m;
+      else if (g >= m) g -= m;
+    } else {
+      g = (int)fixed_coord(q, s, f.r_fixed, f.modulus);
+    }
+    *cell = g >> kFracBits;
+    *frac = (g >> (kFracBits - 14)) & (kWeightOne - 1);
+  } else {
+    const long long g = fixed_coord(q, s, f.r_fixed, f.modulus);
+    *cell = (int)(g >> kFracBits);
+    *frac = (int)((g >> (kFracBits - 14)) & (kWeightOne - 1));
+  }
+}
 #endif
 
 #ifdef __CUDACC__
@@ -280,6 +317,9 @@ int launch_pk_bins(const Grid3& g, const float2* dk, const long long* edges, int
 int launch_pk_finish(const double* partials, int nblocks, int nbins, const double* geom, double kfund, double pscale,
                      double shot, double* pk, cudaStream_t st);
 int launch_dense_spectrum(const Grid3& g, const float2* src, float* dst, cudaStream_t st);
+// out[3][m] = the three real force fields f (rows of 2 pc floats) at mesh cells (ix N + iy) N + iz.
+int launch_sample_mesh(const Grid3& g, const float* const f[3], const long long* cells, long long m, float* out,
+                       cudaStream_t st);
 
 }  // namespace cola
 

@@ -29,8 +29,6 @@ unsigned grid_for(long long work, int threads) {
   return (unsigned)(b < 1 ? 1 : b);
 }
 
-// Fixed-point mesh coordinate of one axis: G = (q R + rint(s 2^20)) mod (N 2^20).  Displacements
-// below one box length wrap with one compare; larger ones take the modulo path.
 // Particles are processed by lattice rows: blockIdx.x (grid-stride) indexes the row (qx, qy) and
 // the threads walk qz, so the lattice index needs one division per row and none per particle.
 constexpr int kRowThreads = 256;
@@ -460,6 +458,22 @@ __global__ void k_pk_finish(const double* __restrict__ partials, int nblocks, in
   }
 }
 
+// out[j m + i] = F_j at mesh cell cells[i] = (ix N + iy) N + iz of the real fields (rows of rs floats)
+__global__ void k_sample_mesh(int n, long long rs, const float* __restrict__ f0, const float* __restrict__ f1,
+                              const float* __restrict__ f2, const long long* __restrict__ cells, long long m,
+                              float* __restrict__ out) {
+  const long long n3 = (long long)n * n * n;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < m; t += (long long)gridDim.x * blockDim.x) {
+    long long c = cells[t];
+    c = c < 0 ? 0 : (c >= n3 ? n3 - 1 : c);   // the host validates the cells; never read outside
+    const long long row = c / n, z = c - row * n;
+    const long long o = row * rs + z;
+    out[t] = f0[o];
+    out[m + t] = f1[o];
+    out[2 * m + t] = f2[o];
+  }
+}
+
 __global__ void k_dense_spectrum(int n, int pc, int nc, const float2* __restrict__ src, float2* dst) {
   const long long total = (long long)n * n * nc;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
@@ -565,6 +579,13 @@ int launch_pk_finish(const double* partials, int nblocks, int nbins, const doubl
                      double shot, double* pk, cudaStream_t st) {
   k_pk_finish<<<1, 128, 0, st>>>(partials, nblocks, nbins, geom, kfund, pscale, shot, pk);
   return check_launch("pk_finish");
+}
+
+int launch_sample_mesh(const Grid3& g, const float* const f[3], const long long* cells, long long m, float* out,
+                       cudaStream_t st) {
+  if (m <= 0) return COLA_OK;
+  k_sample_mesh<<<grid_for(m, 256), 256, 0, st>>>(g.n, 2LL * g.pc, f[0], f[1], f[2], cells, m, out);
+  return check_launch("sample_mesh");
 }
 
 int launch_dense_spectrum(const Grid3& g, const float2* src, float* dst, cudaStream_t st) {

@@ -1,0 +1,101 @@
+"""The benchmark's mesh size (1536^3) and its kernel schedules, checked element by element against the
+FP64 oracle: the density is a sum of plane waves (given to the library as its fixed-point mesh, in
+place of the deposit), whose spectrum and force the oracle states in closed form
+(``oracle.pm.plane_wave_spectrum`` / ``plane_wave_force``, pinned to the oracle's FFT path on small
+meshes).  Every element of the forward spectrum is compared (the waves' modes to their closed form,
+all others to zero); the three force fields at 2^20 sampled cells and along whole rows of each axis.
+The schedules are the size-based default and the one the benchmark's autotuner picks at this size
+(in-place pipelined strided passes, tiles of 8 pencils for the Green pass, 8-element C2R passes),
+so the kernels the benchmark times are the kernels checked here."""
+
+import math
+
+import numpy as np
+import pytest
+
+from oracle import cosmology, pm
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+NP, BOX = 256, 1200.0
+WAVES = [((1, 0, 0), 0.2, 0.3), ((3, -2, 5), 0.1, -1.1), ((-40, 57, 0), 0.15, 2.0), ((0, 0, 767), 0.05, 0.7),
+         ((613, -700, 129), 0.1, -2.5), ((-255, 384, 511), 0.08, 1.3)]
+SCHEDULES = [None, 6215]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    free, _ = torch.cuda.mem_get_info()
+    if free < 150 * 2 ** 30:
+        pytest.skip("needs about 150 GB of free device memory")
+    from paper_1507_05329_gb300 import build
+    build.build()
+
+
+def plane_wave_mesh(n, n_particles, waves, device="cuda"):
+    """The fixed-point mesh rho = rint(C (1 + delta)), C = n_particles 2^42 / N^3, of the waves' delta,
+    built x-plane by x-plane in FP64 (an input; the expected values come from the oracle)."""
+    c = n_particles * 2.0 ** 42 / n ** 3
+    rho = torch.empty((n, n, n), dtype=torch.int64, device=device)
+    iy = torch.arange(n, device=device, dtype=torch.float64).view(n, 1)
+    iz = torch.arange(n, device=device, dtype=torch.float64).view(1, n)
+    for x0 in range(0, n, 64):
+        ix = torch.arange(x0, min(x0 + 64, n), device=device, dtype=torch.float64).view(-1, 1, 1)
+        d = torch.zeros((ix.shape[0], n, n), dtype=torch.float64, device=device)
+        for m, amp, phi in waves:
+            d += amp * torch.cos(2.0 * math.pi * (m[0] * ix + m[1] * iy + m[2] * iz) / n + phi)
+        rho[x0:x0 + ix.shape[0]] = torch.round(c * (1.0 + d)).to(torch.int64)
+    return rho
+
+
+@pytest.fixture(scope="module")
+def setup():
+    from paper_1507_05329_gb300 import Context, Params
+    n = 1536
+    ctx = Context(Params(np_side=NP, nmesh=n, box=BOX))
+    rho = plane_wave_mesh(n, NP ** 3, WAVES)
+    yield ctx, rho, n
+    ctx.close()
+
+
+@pytest.mark.parametrize("sched", SCHEDULES)
+def test_fullsize_spectrum_every_element(setup, sched):
+    ctx, rho, n = setup
+    if sched is not None:
+        ctx.schedule = sched
+    dk = ctx.density_spectrum_of_mesh(rho)
+    ctx.sync()
+    sparse = pm.plane_wave_spectrum(WAVES, n)
+    peak = max(abs(v) for v in sparse.values())
+    for key, val in sparse.items():
+        got = dk[key].double().cpu().numpy()
+        assert abs(complex(got[0], got[1]) - val) <= 5e-6 * abs(val), (key, got, val)
+        dk[key] = 0.0
+    rest = float(dk.abs().max())            # every other mode of the oracle's spectrum is zero
+    assert rest <= 2e-6 * peak, rest / peak
+
+
+@pytest.mark.parametrize("sched", SCHEDULES)
+def test_fullsize_force_against_oracle(setup, sched):
+    ctx, rho, n = setup
+    if sched is not None:
+        ctx.schedule = sched
+    a = 0.37
+    fs = 1.5 * 0.27 / a
+    g = np.random.default_rng(5)
+    cells = [g.integers(0, n ** 3, size=1 << 20)]
+    for axis_stride, (u, v) in ((1, (17, 1201)), (n, (5, 900)), (n * n, (1535, 3))):   # whole rows along z, y, x
+        base = (u * n + v) * n if axis_stride == 1 else ((u * n + v) if axis_stride == n * n else u * n * n + v)
+        cells.append(base + axis_stride * np.arange(n))
+    cells = np.concatenate(cells).astype(np.int64)
+    got = ctx.pm_force_of_mesh(rho, a, torch.from_numpy(cells).cuda())
+    ctx.sync()
+    got = got.double().cpu().numpy()
+    ref = pm.plane_wave_force(WAVES, n, fs, cells)
+    scale = np.abs(ref).max()
+    err = np.abs(got - ref)
+    assert err.max() <= 2e-5 * scale, err.max() / scale
+    assert math.sqrt(np.mean(err ** 2)) <= 3e-6 * scale, math.sqrt(np.mean(err ** 2)) / scale

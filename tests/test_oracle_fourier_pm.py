@@ -84,3 +84,26 @@ def test_pair_force_tends_to_newtonian():
         ratio[r] = float(np.mean(np.concatenate(vals)))
     assert ratio[1.0] < 0.9                      # softened inside a cell
     assert abs(ratio[3.0] - 1.0) < 0.03 and abs(ratio[4.0] - 1.0) < 0.02
+
+
+# ---- the plane-wave closed forms used at full mesh size, pinned to the oracle's FFT path -----------
+WAVES = [((1, 0, 0), 0.2, 0.3), ((3, -2, 5), 0.1, -1.1), ((-4, 5, 0), 0.15, 2.0), ((0, 0, 7), 0.05, 0.7),
+         ((6, 7, -3), 0.1, -2.5)]
+
+
+@pytest.mark.parametrize("n", [16, 18])
+def test_plane_wave_closed_forms_match_the_fft_path(n):
+    from oracle import fourier, pm
+    cells = np.arange(n ** 3)
+    delta = pm.plane_wave_density(WAVES, n, cells).reshape(n, n, n)
+    dk = fourier.rfft3(delta)
+    sparse = pm.plane_wave_spectrum(WAVES, n)
+    expect = np.zeros_like(dk)
+    for key, val in sparse.items():
+        expect[key] = val
+    np.testing.assert_allclose(dk, expect, atol=1e-9 * n ** 3)
+    f = pm.force_mesh(delta, 1.37).reshape(3, -1)
+    np.testing.assert_allclose(pm.plane_wave_force(WAVES, n, 1.37, cells), f, rtol=0, atol=1e-12)
+    # a wave on the k_z = 0 plane is stored twice (+m and -m); others once
+    assert ((-4) % n, 5, 0) in sparse and (4, (-5) % n, 0) in sparse
+    assert (3, (-2) % n, 5) in sparse and ((-3) % n, 2, (-5) % n) not in sparse
