@@ -4,9 +4,10 @@ place of the deposit), whose spectrum and force the oracle states in closed form
 (``oracle.pm.plane_wave_spectrum`` / ``plane_wave_force``, pinned to the oracle's FFT path on small
 meshes).  Every element of the forward spectrum is compared (the waves' modes to their closed form,
 all others to zero); the three force fields at 2^20 sampled cells and along whole rows of each axis.
-The schedules are the size-based default and the one the benchmark's autotuner picks at this size
-(in-place pipelined strided passes, tiles of 8 pencils for the Green pass, 8-element C2R passes),
-so the kernels the benchmark times are the kernels checked here."""
+The schedules are the size-based default and the one the benchmark's autotuner picks at 1536
+(in-place pipelined strided passes, the pipelined Green pass on tiles of 8 pencils, 8-element C2R
+passes), so the kernels the benchmark times are the kernels checked here; 1024 and 1280 cover the
+other radix plans of those kernels."""
 
 import math
 
@@ -19,9 +20,15 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 NP, BOX = 256, 1200.0
-WAVES = [((1, 0, 0), 0.2, 0.3), ((3, -2, 5), 0.1, -1.1), ((-40, 57, 0), 0.15, 2.0), ((0, 0, 767), 0.05, 0.7),
-         ((613, -700, 129), 0.1, -2.5), ((-255, 384, 511), 0.08, 1.3)]
 SCHEDULES = [None, 6215]
+
+
+def waves_for(n):
+    """Plane waves reaching every radix digit of an n-point transform: low modes, a k_z = 0 wave (stored
+    twice in the half spectrum), the highest k_z below Nyquist and modes near |m| = n/2."""
+    h = n // 2
+    return [((1, 0, 0), 0.2, 0.3), ((3, -2, 5), 0.1, -1.1), ((-40, 57, 0), 0.15, 2.0), ((0, 0, h - 1), 0.05, 0.7),
+            ((h * 4 // 5, -(h - 68), h // 6), 0.1, -2.5), ((-(h // 3), h // 2, h * 2 // 3), 0.08, 1.3)]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -51,24 +58,29 @@ def plane_wave_mesh(n, n_particles, waves, device="cuda"):
     return rho
 
 
-@pytest.fixture(scope="module")
-def setup():
+@pytest.fixture(scope="module", params=[1536, 1280, 1024])
+def setup(request):
+    """The three mesh sizes whose passes run on tiles of 8 pencils (in-place pipelined y passes and the
+    pipelined Green pass): radix plans 16 16 6, 16 16 5 and 16 8 8."""
     from paper_1507_05329_gb300 import Context, Params
-    n = 1536
+    n = request.param
     ctx = Context(Params(np_side=NP, nmesh=n, box=BOX))
-    rho = plane_wave_mesh(n, NP ** 3, WAVES)
-    yield ctx, rho, n
+    waves = waves_for(n)
+    rho = plane_wave_mesh(n, NP ** 3, waves)
+    yield ctx, rho, n, waves
     ctx.close()
+    del rho
+    torch.cuda.empty_cache()
 
 
 @pytest.mark.parametrize("sched", SCHEDULES)
 def test_fullsize_spectrum_every_element(setup, sched):
-    ctx, rho, n = setup
+    ctx, rho, n, waves = setup
     if sched is not None:
         ctx.schedule = sched
     dk = ctx.density_spectrum_of_mesh(rho)
     ctx.sync()
-    sparse = pm.plane_wave_spectrum(WAVES, n)
+    sparse = pm.plane_wave_spectrum(waves, n)
     peak = max(abs(v) for v in sparse.values())
     for key, val in sparse.items():
         got = dk[key].double().cpu().numpy()
@@ -80,21 +92,21 @@ def test_fullsize_spectrum_every_element(setup, sched):
 
 @pytest.mark.parametrize("sched", SCHEDULES)
 def test_fullsize_force_against_oracle(setup, sched):
-    ctx, rho, n = setup
+    ctx, rho, n, waves = setup
     if sched is not None:
         ctx.schedule = sched
     a = 0.37
     fs = 1.5 * 0.27 / a
     g = np.random.default_rng(5)
     cells = [g.integers(0, n ** 3, size=1 << 20)]
-    for axis_stride, (u, v) in ((1, (17, 1201)), (n, (5, 900)), (n * n, (1535, 3))):   # whole rows along z, y, x
+    for axis_stride, (u, v) in ((1, (17, n - 335)), (n, (5, n - 636)), (n * n, (n - 1, 3))):   # whole rows along z, y, x
         base = (u * n + v) * n if axis_stride == 1 else ((u * n + v) if axis_stride == n * n else u * n * n + v)
         cells.append(base + axis_stride * np.arange(n))
     cells = np.concatenate(cells).astype(np.int64)
     got = ctx.pm_force_of_mesh(rho, a, torch.from_numpy(cells).cuda())
     ctx.sync()
     got = got.double().cpu().numpy()
-    ref = pm.plane_wave_force(WAVES, n, fs, cells)
+    ref = pm.plane_wave_force(waves, n, fs, cells)
     scale = np.abs(ref).max()
     err = np.abs(got - ref)
     assert err.max() <= 2e-5 * scale, err.max() / scale
