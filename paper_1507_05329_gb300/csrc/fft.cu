@@ -363,26 +363,6 @@ int launch_green_x(const FftPlan& p, const Grid3& g, const float2* in, float2* c
   const double n3 = (double)g.n * g.n * g.n;
   const float g_scale = (float)((double)scale / (kf * kf * n3));
   FastPlan fp;
-  if (fast_plan(p, &fp) && p.pipe_inplace && p.green_ept == 16 && fp.nst >= 2 && g.n * 8 <= kWideElems && g.nc >= 8) {
-    // persistent pipelined pass with one inverse transform (F_x by the real-space 4-point stencil):
-    // tiles of 8 pencils in the in-place pipe's two buffers
-    const int lw = 3;
-    int th = ((g.n << lw) + kEpt - 1) / kEpt;
-    th = ((th + 31) / 32) * 32;
-    const size_t smem = 2 * (size_t)(g.n + g.n / 16 + 1) * 8 * sizeof(float2);
-    if (th <= kPipeThreads && (long long)th * kEpt >= (long long)(g.n << lw) && smem <= (size_t)kInplaceKb * 1024) {
-      const int nchunks = (g.nc + 7) >> 3, ntiles = nchunks * g.n;
-      int dev = 0, sms = 152;
-      if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-      const int ctas = ntiles < sms ? ntiles : sms;
-      const bool launched =
-          max_radix(fp) > 8 ? green_pipe_launch<16>(fp, lw, ctas, th, smem, in, out, g.pc, g.nc, dtab, g_scale, nchunks,
-                                                    ntiles, st)
-                            : green_pipe_launch<8>(fp, lw, ctas, th, smem, in, out, g.pc, g.nc, dtab, g_scale, nchunks,
-                                                   ntiles, st);
-      if (launched) return check_launch("green_pipe");
-    }
-  }
   if (fast_plan(p, &fp)) {
     if (p.green_ept == 8 && g.n <= kTileElems / 2) {
       // half the elements per thread: tiles of at most 3072 elements keep 384 threads

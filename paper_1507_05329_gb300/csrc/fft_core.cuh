@@ -945,11 +945,6 @@ void fast_green_launch(const fftk::FastPlan& fp, int lw, dim3 grid, int threads,
 template <int MAXR>
 void c2r_pipe_launch(const fftk::FastPlan& fp, int lw, int ctas, int threads, size_t smem, int ept, float2* data, int pc,
                      long long nrows, long long ntiles, cudaStream_t st);
-// false (nothing launched) for plans it has no instance for
-template <int MAXR>
-bool green_pipe_launch(const fftk::FastPlan& fp, int lw, int ctas, int threads, size_t smem, const float2* in,
-                       float2* const out[3], int pc, int nc, const float* dtab, float g_scale, int nchunks, int ntiles,
-                       cudaStream_t st);
 template <int MAXR>
 void pipe_pencils_launch(const fftk::FastPlan& fp, int lw, int ctas, int threads, size_t smem, int dir, int ept,
                          bool inplace, float2* data, long long jstride, long long ostride, int nc, int nchunks,
