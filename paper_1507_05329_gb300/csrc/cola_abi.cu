@@ -162,10 +162,15 @@ int deposit_and_forward_yz(cola_ctx* c, const float* s) {
 }
 
 // S3 after forward_yz: the three force components as real fields in cbuf[0..2] (rows of 2 pc floats).
-int green_and_inverse(cola_ctx* c, double force_scale) {
+// With save_spectrum the fast Green kernels also leave the density's forward spectrum in the
+// (already consumed) fixed-point mesh buffer and c->spec_saved says so.
+int green_and_inverse(cola_ctx* c, double force_scale, bool save_spectrum = false) {
   const Grid3& g = c->mesh;
   float2* const outs[3] = {c->cbuf[0], c->cbuf[1], c->cbuf[2]};
-  COLA_TRY(STAGED(kStGreenX, launch_green_x(c->mplan, g, c->cbuf[2], outs, c->dtab, (float)force_scale, c->stream)));
+  bool saved = false;
+  COLA_TRY(STAGED(kStGreenX, launch_green_x(c->mplan, g, c->cbuf[2], outs, c->dtab, (float)force_scale, c->stream,
+                                            save_spectrum ? reinterpret_cast<float2*>(c->rho) : nullptr, &saved)));
+  c->spec_saved = saved;
   for (int j = 0; j < 3; ++j) {
     COLA_TRY(STAGED(kStInvY, launch_pencils(c->mplan, g, 1, +1, c->cbuf[j], c->stream)));
     COLA_TRY(STAGED(kStInvZ, launch_c2r_rows(c->mplan, g, c->cbuf[j], c->stream)));
@@ -174,9 +179,9 @@ int green_and_inverse(cola_ctx* c, double force_scale) {
 }
 
 // S1-S3: the three force components as real fields in cbuf[0..2] (rows of 2 pc floats).
-int force_mesh(cola_ctx* c, const float* s, double force_scale) {
+int force_mesh(cola_ctx* c, const float* s, double force_scale, bool save_spectrum = false) {
   COLA_TRY(deposit_and_forward_yz(c, s));
-  return green_and_inverse(c, force_scale);
+  return green_and_inverse(c, force_scale, save_spectrum);
 }
 
 int inverse3d(cola_ctx* c, const Grid3& g, const FftPlan& p, float2* b) {
@@ -509,20 +514,20 @@ extern "C" int cola_pm_force(cola_ctx* c, const float* s, double a, float* force
   return gather(c, s, force, nullptr, nullptr, nullptr, nullptr, nullptr);
 }
 
-extern "C" int cola_step(cola_ctx* c, int i, float* s, float* v, const float* psi1, const float* psi2) {
+namespace {
+// COLA step i; save_spectrum keeps the density spectrum of s (see green_and_inverse).
+int step_impl(cola_ctx* c, int i, float* s, float* v, const float* psi1, const float* psi2, bool save_spectrum) {
   if (!c || i < 1 || i > c->p.nstep) return COLA_ERR_INVALID;
   for (const void* p : {(const void*)s, (const void*)v, (const void*)psi1, (const void*)psi2})
     COLA_TRY(check_ptr(p));
   const StepScalars& ss = c->steps[i];
-  COLA_TRY(force_mesh(c, s, ss.force_scale));
+  COLA_TRY(force_mesh(c, s, ss.force_scale, save_spectrum));
   const KickDrift kd{(float)ss.kick, (float)ss.drift, (float)ss.dd1, (float)ss.dd2, (float)ss.c1, (float)ss.c2};
   return gather(c, nullptr, nullptr, s, v, psi1, psi2, &kd);
 }
 
-extern "C" int cola_power_spectrum_ex(cola_ctx* c, const float* s, double* pk, int nbins, int flags) {
-  if (!c || nbins < 1 || nbins > kPkMaxBins || (flags & ~COLA_PK_CIC_CORRECT)) return COLA_ERR_INVALID;
-  COLA_TRY(check_ptr(s));
-  COLA_TRY(check_ptr(pk));
+// S6 binning of a forward density spectrum dk (complex N x N x pc) into pk.
+int pk_from_spectrum(cola_ctx* c, const float2* dk, double* pk, int nbins, int flags) {
   if (nbins != c->edges_nbins) {
     // the pinned host copy may still feed an earlier upload: wait for it before rewriting it
     COLA_TRY(cuda_status(cudaStreamSynchronize(c->stream), "pk edges"));
@@ -531,8 +536,6 @@ extern "C" int cola_power_spectrum_ex(cola_ctx* c, const float* s, double* pk, i
                                          cudaMemcpyHostToDevice, c->stream), "edges"));
     c->edges_nbins = nbins;
   }
-  COLA_TRY(deposit_and_forward_yz(c, s));
-  COLA_TRY(STAGED(kStFwdX, launch_pencils(c->mplan, c->mesh, 0, -1, c->cbuf[2], c->stream)));
   const double nn = c->mesh.n;
   const double vol = std::pow(c->p.box, 3);
   const double pscale = vol / (nn * nn * nn * nn * nn * nn);
@@ -543,10 +546,24 @@ extern "C" int cola_power_spectrum_ex(cola_ctx* c, const float* s, double* pk, i
                                               c->stream)));
     c->pk_geom_nbins = nbins;
   }
-  COLA_TRY(STAGED(kStPk, launch_pk_bins(c->mesh, c->cbuf[2], c->edges, nbins, corr, c->pk_partials, c->pk_blocks,
+  COLA_TRY(STAGED(kStPk, launch_pk_bins(c->mesh, dk, c->edges, nbins, corr, c->pk_partials, c->pk_blocks,
                                         c->stream)));
   return STAGED(kStPk, launch_pk_finish(c->pk_partials, c->pk_blocks, nbins, c->pk_geom, kfund, pscale,
                                         corr ? vol / (double)c->pg.npart : 0.0, pk, c->stream));
+}
+}  // namespace
+
+extern "C" int cola_step(cola_ctx* c, int i, float* s, float* v, const float* psi1, const float* psi2) {
+  return step_impl(c, i, s, v, psi1, psi2, false);
+}
+
+extern "C" int cola_power_spectrum_ex(cola_ctx* c, const float* s, double* pk, int nbins, int flags) {
+  if (!c || nbins < 1 || nbins > kPkMaxBins || (flags & ~COLA_PK_CIC_CORRECT)) return COLA_ERR_INVALID;
+  COLA_TRY(check_ptr(s));
+  COLA_TRY(check_ptr(pk));
+  COLA_TRY(deposit_and_forward_yz(c, s));
+  COLA_TRY(STAGED(kStFwdX, launch_pencils(c->mplan, c->mesh, 0, -1, c->cbuf[2], c->stream)));
+  return pk_from_spectrum(c, c->cbuf[2], pk, nbins, flags);
 }
 
 extern "C" int cola_power_spectrum(cola_ctx* c, const float* s, double* pk, int nbins) {
@@ -580,9 +597,16 @@ extern "C" int cola_snapshot(cola_ctx* c, int i, double a_snap, const float* s, 
 extern "C" int cola_run(cola_ctx* c, const float* wn, float* s, float* v, float* psi1, float* psi2, double* pk,
                         int nbins) {
   if (!c) return COLA_ERR_INVALID;
+  if (pk && (nbins < 1 || nbins > kPkMaxBins || check_ptr(pk) != COLA_OK)) return COLA_ERR_INVALID;
   COLA_TRY(cola_ic_2lpt(c, wn, s, v, psi1, psi2));
-  for (int i = 1; i <= c->p.nstep; ++i) COLA_TRY(cola_step(c, i, s, v, psi1, psi2));
-  if (pk) COLA_TRY(cola_power_spectrum(c, s, pk, nbins));
+  for (int i = 1; i < c->p.nstep; ++i) COLA_TRY(step_impl(c, i, s, v, psi1, psi2, false));
+  // the last step kicks to a = 1 without drifting, so the positions it deposits are the final ones:
+  // its density spectrum, kept by the Green pass, gives P(k) without a second deposit and FFT
+  COLA_TRY(step_impl(c, c->p.nstep, s, v, psi1, psi2, pk != nullptr));
+  if (pk) {
+    if (c->spec_saved) COLA_TRY(pk_from_spectrum(c, reinterpret_cast<const float2*>(c->rho), pk, nbins, 0));
+    else COLA_TRY(cola_power_spectrum(c, s, pk, nbins));
+  }
   return COLA_OK;
 }
 

@@ -106,9 +106,11 @@ int launch_pencils(const FftPlan& p, const Grid3& g, int axis, int dir, float2* 
                    cudaStream_t st);
 // Forward x transform, then for each j in {x, y, z}: out_j = i D(k_j) scale delta(k)/k^2
 // (k in rad/cell, D the 4-point gradient kernel), then the inverse x transform of out_j.
-// out[2] may alias in.
+// out[2] may alias in.  With spec_out (a complex grid that aliases none of the others) the fast
+// kernels also write the forward spectrum delta(k) there and set *spec_saved.
 int launch_green_x(const FftPlan& p, const Grid3& g, const float2* in, float2* const out[3],
-                   const float* dtab, float scale, cudaStream_t st);
+                   const float* dtab, float scale, cudaStream_t st, float2* spec_out = nullptr,
+                   bool* spec_saved = nullptr);
 
 // Launchers (particles.cu).
 struct ParticleGeom {
@@ -346,6 +348,7 @@ struct cola_ctx {
   int pk_blocks = 0;
   double* pk_geom = nullptr;              // [2][nbins]: sum of |m| and mode count per bin
   int pk_geom_nbins = 0;                  // bins the geometry was computed for (0: none yet)
+  bool spec_saved = false;                // the last force evaluation left delta(k) in the rho buffer
   int* flags = nullptr;                   // sticky device error flags
   unsigned long long* mass_acc = nullptr; // 128-bit total of the fixed-point mesh (overflow check)
   bool binned = false;                    // tile-wise deposit (else direct atomics)

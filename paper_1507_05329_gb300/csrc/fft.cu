@@ -358,7 +358,8 @@ int launch_pencils(const FftPlan& p, const Grid3& g, int axis, int dir, float2* 
 }
 
 int launch_green_x(const FftPlan& p, const Grid3& g, const float2* in, float2* const out[3],
-                   const float* dtab, float scale, cudaStream_t st) {
+                   const float* dtab, float scale, cudaStream_t st, float2* spec_out, bool* spec_saved) {
+  if (spec_saved) *spec_saved = false;
   const double kf = 2.0 * M_PI / g.n;
   const double n3 = (double)g.n * g.n * g.n;
   const float g_scale = (float)((double)scale / (kf * kf * n3));
@@ -373,18 +374,20 @@ int launch_green_x(const FftPlan& p, const Grid3& g, const float2* in, float2* c
       th = ((th + 31) / 32) * 32;
       dim3 grid((g.nc + (1 << t.lw) - 1) >> t.lw, g.n);
       if (max_radix(fp) > 8)
-        fast_green_launch<16, 8>(fp, t.lw, grid, th, t.smem, in, out, g.pc, g.nc, dtab, g_scale, st);
+        fast_green_launch<16, 8>(fp, t.lw, grid, th, t.smem, in, out, g.pc, g.nc, dtab, g_scale, spec_out, st);
       else
-        fast_green_launch<8, 8>(fp, t.lw, grid, th, t.smem, in, out, g.pc, g.nc, dtab, g_scale, st);
+        fast_green_launch<8, 8>(fp, t.lw, grid, th, t.smem, in, out, g.pc, g.nc, dtab, g_scale, spec_out, st);
+      if (spec_saved) *spec_saved = spec_out != nullptr;
       return check_launch("green_fast8");
     }
     const int nbuf = fp.nst >= 3 ? 2 : 1;
     const TileShape t = wide_shape(p, g, fast_shape(g.n, largest_pow2_le(g.nc), nbuf), nbuf);
     dim3 grid((g.nc + (1 << t.lw) - 1) >> t.lw, g.n);
     if (max_radix(fp) > 8)
-      fast_green_launch<16, 16>(fp, t.lw, grid, t.threads, t.smem, in, out, g.pc, g.nc, dtab, g_scale, st);
+      fast_green_launch<16, 16>(fp, t.lw, grid, t.threads, t.smem, in, out, g.pc, g.nc, dtab, g_scale, spec_out, st);
     else
-      fast_green_launch<8, 16>(fp, t.lw, grid, t.threads, t.smem, in, out, g.pc, g.nc, dtab, g_scale, st);
+      fast_green_launch<8, 16>(fp, t.lw, grid, t.threads, t.smem, in, out, g.pc, g.nc, dtab, g_scale, spec_out, st);
+    if (spec_saved) *spec_saved = spec_out != nullptr;
     return check_launch("green_fast");
   }
   const TileShape t = tile_shape(g.n, largest_pow2_le(g.nc));

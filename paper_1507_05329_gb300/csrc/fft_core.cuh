@@ -795,7 +795,7 @@ __device__ __forceinline__ void green_inverse(const FastPlan& p, int lw, const f
 template <int RL, int MAXR, int EPT>
 __device__ __forceinline__ void green_body(const FastPlan& p, int lw, const float2* in, float2* out0, float2* out1,
                                            float2* out2, int pc, int nc, const float* __restrict__ dtab,
-                                           float g_scale) {
+                                           float g_scale, float2* spec_out) {
   extern __shared__ float2 sm[];
   constexpr int kB = (EPT + RL - 1) / RL;
   const int n = p.n, tid = threadIdx.x, nt = blockDim.x, m = p.nst;
@@ -834,6 +834,10 @@ __device__ __forceinline__ void green_body(const FastPlan& p, int lw, const floa
         for (int r = 1; r < RL; ++r) spec[i][r] = cmul(spec[i][r], twid<-1>(p.tw, r * bb * tstr));
       }
       Dft<RL, -1>::run(spec[i]);
+      if (spec_out && w < nc - col0) {   // the forward spectrum itself, for a P(k) of the same density
+#pragma unroll
+        for (int r = 0; r < RL; ++r) spec_out[(long long)(bb + (r << ls)) * jstride + boff + w] = spec[i][r];
+      }
       // element j = bb + r*ns_last: multiply by g_scale / |m|^2 (the common factor of F_j)
       const int my = y < n / 2 ? y : y - n, mz = col0 + w;
 #pragma unroll
@@ -941,7 +945,8 @@ void fast_pencils_launch(const fftk::FastPlan& fp, int lw, dim3 grid, int thread
                          long long jstride, long long ostride, int nc, cudaStream_t st);
 template <int MAXR, int EPT>
 void fast_green_launch(const fftk::FastPlan& fp, int lw, dim3 grid, int threads, size_t smem, const float2* in,
-                       float2* const out[3], int pc, int nc, const float* dtab, float g_scale, cudaStream_t st);
+                       float2* const out[3], int pc, int nc, const float* dtab, float g_scale, float2* spec_out,
+                       cudaStream_t st);
 template <int MAXR>
 void c2r_pipe_launch(const fftk::FastPlan& fp, int lw, int ctas, int threads, size_t smem, int ept, float2* data, int pc,
                      long long nrows, long long ntiles, cudaStream_t st);

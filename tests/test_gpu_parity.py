@@ -252,3 +252,22 @@ def test_overflow_is_reported():
         ctx.sync()
     assert e.value.status == 4
     del rho
+
+
+@pytest.mark.parametrize("npd,nm", [(32, 64), (16, 60), (24, 96)])
+def test_run_power_spectrum_equals_power_spectrum_of_final_positions(npd, nm):
+    """cola_run takes P(k) from the last step's density spectrum (the last step does not drift, so it
+    deposits the final positions); that equals cola_power_spectrum of the returned positions: counts and
+    mean |k| exactly, P to the FP32 rounding of two FFT kernels.  60 exercises the generic-plan path,
+    which recomputes the spectrum instead."""
+    from paper_1507_05329_gb300 import Context, Params
+    ctx = Context(Params(box=200.0, np_side=npd, nmesh=nm, seed=21))
+    out = ctx.run(None, nbins=32)
+    again = ctx.power_spectrum(out["s"], 32)
+    ctx.sync()
+    a, b = out["pk"].cpu().numpy(), again.cpu().numpy()
+    assert np.array_equal(a[2], b[2])
+    m = b[2] > 0
+    np.testing.assert_array_equal(a[0][m], b[0][m])
+    np.testing.assert_allclose(a[1][m], b[1][m], rtol=2e-6)
+    ctx.close()
