@@ -251,15 +251,17 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const unsigned* __r
   }
 }
 
-// Tile-wise deposit by shared-memory atomics: accumulator [T][T][TZ] of 64-bit fixed-point sums
-// (two 32-bit atomics with carry per CIC corner).  The tile's primary and spill entries form one index
-// range, so a CTA's threads run out of work together.  Any entry count; the fallback of the pull below.
+// Tile-wise deposit: shared accumulator [T][T][TZ] of 64-bit fixed-point sums.  The tile's primary
+// and spill entries form one index range, so a CTA's threads run out of work together.
 template <int LT, int LZ, bool F32>
-__device__ __forceinline__ void deposit_atomic(unsigned long long* acc, const ParticleGeom& pg, const BinGeom& b,
-                                               const FixedGeo& fg, const float* __restrict__ s,
-                                               const unsigned* __restrict__ off_p, const unsigned* __restrict__ ent_p,
-                                               const unsigned* __restrict__ off_s, const unsigned* __restrict__ ent_s,
-                                               unsigned long long* rho) {
+__global__ void __launch_bounds__(kThreads, COLA_DEPOSIT_MIN_BLOCKS) k_deposit_tiles(ParticleGeom pg, BinGeom b, FixedGeo fg,
+                                                           const float* __restrict__ s,
+                                                           const unsigned* __restrict__ off_p,
+                                                           const unsigned* __restrict__ ent_p,
+                                                           const unsigned* __restrict__ off_s,
+                                                           const unsigned* __restrict__ ent_s,
+                                                           unsigned long long* rho) {
+  extern __shared__ unsigned long long acc[];
   const int lt = LT ? LT : b.lt, lz = LZ ? LZ : b.lz;
   const int nm = pg.n, T = 1 << lt, TZ = 1 << lz;
   const int tile = blockIdx.x;
@@ -321,164 +323,6 @@ __device__ __forceinline__ void deposit_atomic(unsigned long long* acc, const Pa
     const int lx = col >> lt, ly = col & (T - 1);
     rho[((long long)(x0 + lx) * nm + (y0 + ly)) * nm + z0 + z] = acc[i];
   }
-}
-
-
-// Tile-wise deposit by a counting sort and a pull, without atomics on the mesh cells.  Every entry
-// (primary or spill) has its base cell (the cell its CIC cloud starts from) in the tile or one cell
-// below it along any axis: the tile's (T+1)^2 (TZ+1) "base cells" with a one-cell lower halo.  The
-// entries are counting-sorted by base cell in shared memory (one atomic per entry to count, one to
-// place it); then each cell of the tile sums, over its 8 lower neighbours (including itself) among the
-// base cells, the integer weights of the particles sorted there for that corner, in a register, and
-// stores the exact 64-bit total once.  The sum is the atomic version's, term for term (integer
-// addition, any order).  Tiles holding more than kPullCap entries take deposit_atomic.
-constexpr int kPullPerThread = 8;                          // entries a thread keeps in registers
-constexpr int kPullCap = kPullPerThread * kThreads;        // 2048 entries per tile
-
-template <int LT, int LZ>
-__host__ __device__ __forceinline__ int pull_bases(const BinGeom& b) {
-  const int T = 1 << (LT ? LT : b.lt), TZ = 1 << (LZ ? LZ : b.lz);
-  return (T + 1) * (T + 1) * (TZ + 1);
-}
-
-// shared memory of the pull: base-cell cursors (4 B) and the sorted entries' weight fractions (8 B)
-size_t pull_smem_bytes(const BinGeom& b) {
-  return ((size_t)pull_bases<0, 0>(b) * 4 + 15) / 16 * 16 + (size_t)kPullCap * 8;
-}
-
-// Exclusive scan of cnt[0..m) in place by one CTA; every thread takes a contiguous run.
-__device__ __forceinline__ void block_scan_inplace(unsigned* cnt, int m) {
-  __shared__ unsigned wsum[kThreads / 32];
-  const int per = (m + blockDim.x - 1) / blockDim.x;
-  const int lo = threadIdx.x * per, hi = lo + per < m ? lo + per : m;
-  unsigned v = 0;
-  for (int i = lo; i < hi; ++i) v += cnt[i];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  unsigned incl = v;
-  for (int d = 1; d < 32; d <<= 1) {
-    const unsigned o = __shfl_up_sync(0xffffffffu, incl, d);
-    if (lane >= d) incl += o;
-  }
-  if (lane == 31) wsum[warp] = incl;
-  __syncthreads();
-  if (warp == 0) {
-    unsigned w = lane < (int)(blockDim.x / 32) ? wsum[lane] : 0;
-    for (int d = 1; d < 32; d <<= 1) {
-      const unsigned o = __shfl_up_sync(0xffffffffu, w, d);
-      if (lane >= d) w += o;
-    }
-    if (lane < (int)(blockDim.x / 32)) wsum[lane] = w;
-  }
-  __syncthreads();
-  unsigned run = (warp ? wsum[warp - 1] : 0) + incl - v;
-  for (int i = lo; i < hi; ++i) {
-    const unsigned c = cnt[i];
-    cnt[i] = run;
-    run += c;
-  }
-}
-
-template <int LT, int LZ, bool F32>
-__device__ __forceinline__ void deposit_pull(unsigned char* smem, const ParticleGeom& pg, const BinGeom& b,
-                                             const FixedGeo& fg, const float* __restrict__ s,
-                                             const unsigned* __restrict__ ent_p, unsigned p0, unsigned np_t,
-                                             const unsigned* __restrict__ ent_s, unsigned s0, unsigned total,
-                                             unsigned long long* rho) {
-  const int lt = LT ? LT : b.lt, lz = LZ ? LZ : b.lz;
-  const int nm = pg.n, T = 1 << lt, TZ = 1 << lz, HX = T + 1, HZ = TZ + 1;
-  const int nbase = pull_bases<LT, LZ>(b);
-  unsigned* cur = reinterpret_cast<unsigned*>(smem);
-  unsigned long long* sorted = reinterpret_cast<unsigned long long*>(smem + ((size_t)nbase * 4 + 15) / 16 * 16);
-  const int tile = blockIdx.x;
-  const int bz = tile % b.nz, bxy = tile / b.nz;
-  const int bx = bxy / b.nt, by = bxy - bx * b.nt;
-  const int x0 = bx << lt, y0 = by << lt, z0 = bz << lz;
-  const int org[3] = {x0, y0, z0}, side[3] = {T, T, TZ};
-  for (int i = threadIdx.x; i < nbase; i += blockDim.x) cur[i] = 0u;
-  __syncthreads();
-  // each entry: base cell (halo coordinates) and its three 14-bit fractions, kept in registers
-  const long long n = pg.npart;
-  unsigned long long key[kPullPerThread];
-#pragma unroll
-  for (int j = 0; j < kPullPerThread; ++j) {
-    key[j] = ~0ULL;
-    const unsigned k = threadIdx.x + j * blockDim.x;
-    if (k < total) {
-      int q[3];
-      long long id;
-      unpack_q(k < np_t ? ent_p[p0 + k] : ent_s[s0 + (k - np_t)], pg.np, q, &id);
-      int h[3], f[3];
-      bool ok = true;
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        int c;
-        cell_frac<F32>(q[a], __ldg(s + a * n + id), fg, &c, &f[a]);
-        int r = c - org[a];
-        if (r >= side[a]) r -= nm;   // the periodic neighbour below the tile at the origin
-        ok = ok && r >= -1 && r < side[a];
-        h[a] = r + 1;
-      }
-      if (ok) {
-        const unsigned hb = (unsigned)((h[0] * HX + h[1]) * HZ + h[2]);
-        key[j] = ((unsigned long long)hb << 42) | ((unsigned long long)f[2] << 28) | ((unsigned long long)f[1] << 14) |
-                 (unsigned long long)f[0];
-        atomicAdd(cur + hb, 1u);
-      }
-    }
-  }
-  __syncthreads();
-  block_scan_inplace(cur, nbase);
-  __syncthreads();
-#pragma unroll
-  for (int j = 0; j < kPullPerThread; ++j) {
-    if (key[j] != ~0ULL) {
-      const unsigned slot = atomicAdd(cur + (unsigned)(key[j] >> 42), 1u);
-      sorted[slot] = key[j] & ((1ULL << 42) - 1);
-    }
-  }
-  __syncthreads();
-  // cur[hb] is now the end of base cell hb's run; its start is cur[hb - 1] (0 for the first)
-  const int cells = (T * T) << lz;
-  for (int i = threadIdx.x; i < cells; i += blockDim.x) {
-    const int col = i >> lz, z = i & (TZ - 1);
-    const int lx = col >> lt, ly = col & (T - 1);
-    unsigned long long sum = 0ULL;
-#pragma unroll
-    for (int d = 0; d < 8; ++d) {
-      const int dx = d >> 2, dy = (d >> 1) & 1, dz = d & 1;
-      const int hb = ((lx + 1 - dx) * HX + (ly + 1 - dy)) * HZ + (z + 1 - dz);
-      const unsigned e0 = hb ? cur[hb - 1] : 0u, e1 = cur[hb];
-      for (unsigned e = e0; e < e1; ++e) {
-        const unsigned long long fr = sorted[e];
-        const unsigned fx = (unsigned)(fr & 0x3FFFu), fy = (unsigned)((fr >> 14) & 0x3FFFu),
-                       fz = (unsigned)((fr >> 28) & 0x3FFFu);
-        const unsigned wxy = (dx ? fx : kWeightOne - fx) * (dy ? fy : kWeightOne - fy);
-        sum += (unsigned long long)wxy * (dz ? fz : kWeightOne - fz);
-      }
-    }
-    rho[((long long)(x0 + lx) * nm + (y0 + ly)) * nm + z0 + z] = sum;
-  }
-}
-
-// One CTA per tile: the pull where the tile's entries fit (and the tile is not its own periodic
-// neighbour), else the shared-memory atomics.
-template <int LT, int LZ, bool F32>
-__global__ void __launch_bounds__(kThreads, COLA_DEPOSIT_MIN_BLOCKS) k_deposit_tiles(ParticleGeom pg, BinGeom b, FixedGeo fg,
-                                                           const float* __restrict__ s,
-                                                           const unsigned* __restrict__ off_p,
-                                                           const unsigned* __restrict__ ent_p,
-                                                           const unsigned* __restrict__ off_s,
-                                                           const unsigned* __restrict__ ent_s,
-                                                           unsigned long long* rho) {
-  extern __shared__ __align__(16) unsigned long long dsm[];
-  const int tile = blockIdx.x;
-  const unsigned p0 = off_p[tile], np_t = off_p[tile + 1] - p0;
-  const unsigned s0 = off_s[tile], total = np_t + (off_s[tile + 1] - s0);
-  if (total <= (unsigned)kPullCap && b.nt > 1 && b.nz > 1)
-    deposit_pull<LT, LZ, F32>(reinterpret_cast<unsigned char*>(dsm), pg, b, fg, s, ent_p, p0, np_t, ent_s, s0, total,
-                              rho);
-  else
-    deposit_atomic<LT, LZ, F32>(dsm, pg, b, fg, s, off_p, ent_p, off_s, ent_s, rho);
 }
 
 // Tile-wise gather (+ kick and drift) over the primary entries of each tile, from a shared copy
@@ -802,9 +646,8 @@ int launch_deposit_tiles(const ParticleGeom& pg, const BinGeom& b, const float* 
   const FixedGeo fg = fixed_geo(pg.n, pg.r_fixed);
   with_instance(b, pg.n, [&](auto lt, auto lz, auto f32) {
     auto k = k_deposit_tiles<decltype(lt)::value, decltype(lz)::value, decltype(f32)::value>;
-    smem_limit(k, 96 * 1024);
-    const size_t sm = bin_smem_bytes(b, pg.n) > pull_smem_bytes(b) ? bin_smem_bytes(b, pg.n) : pull_smem_bytes(b);
-    k<<<b.tiles, kThreads, sm, st>>>(pg, b, fg, s, bb.off_p, bb.ent_p, bb.off_s, bb.ent_s, rho);
+    smem_limit(k, 64 * 1024);
+    k<<<b.tiles, kThreads, bin_smem_bytes(b, pg.n), st>>>(pg, b, fg, s, bb.off_p, bb.ent_p, bb.off_s, bb.ent_s, rho);
   });
   return check_launch("deposit_tiles");
 }
