@@ -621,6 +621,8 @@ def run_ours(args):
         per_stage["bin"] = {"avg_ms": round(prof["bin"][0] / prof["bin"][1], 4), "launches": prof["bin"][1],
                             "note": "particle binning by mesh tiles (implementation overhead, not algorithmic bytes)"}
     pm_ms = sum(prof[k][0] for k in sb) / args.steps
+    # every stage's device time per realisation (2LPT, PM steps, P(k)), CUDA events inside the timed region
+    per_realisation = {k: round(v[0] / args.steps, 3) for k, v in prof.items() if v[1]}
 
     # end to end through the public API with host buffers (pinned), copies inside the timed region.
     # Realisation k's white noise goes in and its s, v, P(k) come out on a copy stream, overlapping the
@@ -697,7 +699,8 @@ def run_ours(args):
                            "pm_step_ms": pm_ms / 10.0, "nbins": args.nbins, "autotune": tuned,
                            "rank_devices": rank_devices},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clocks, "stages": per_stage, "adjoint": adj, "batched": batched}
+                "clocks": clocks, "stages": per_stage, "ms_per_realisation_by_stage": per_realisation,
+                "adjoint": adj, "batched": batched}
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()

@@ -125,7 +125,7 @@ def test_snapshot_run_ends_like_a_plain_run(snapshot_run):
     assert np.array_equal(got["pk_snap"][-1], plain["pk"])
 
 
-@pytest.mark.parametrize("nstep", [20, 50])
+@pytest.mark.parametrize("nstep", [20, 50, 100])
 def test_nstep_sweep(nstep):
     """The paper's step-count study: a 16^3 / 32^3 run with 20 and 50 COLA steps against the oracle,
     final positions within 1e-3 cells RMS."""

@@ -82,7 +82,7 @@ def test_snapshot_rejects_times_outside_the_step():
         cola.snapshot(3, s, v, psi1, psi2, P, 0.45)
 
 
-@pytest.mark.parametrize("nstep", [20, 50])
+@pytest.mark.parametrize("nstep", [20, 50, 100])
 def test_more_steps_converge_to_the_same_free_motion(nstep):
     """n_step sweep (the paper varies the number of steps): the 2LPT-only trajectory (exact force
     F = F_2LPT) is independent of n_step and ends at D1(1) Psi1 + D2(1) Psi2."""
