@@ -343,20 +343,6 @@ __device__ __forceinline__ int gather_floats_t(const BinGeom& b) {
   return 3 * hx * hx * hp;
 }
 
-// Launch order of the one-CTA-per-tile gather: z fastest, then x within groups of kGatherGroupX tiles,
-// then y, then the x groups.  Neighbouring tiles share the halo planes of their staged forces; in this
-// order the x neighbour runs nz launches later and the y neighbour about kGatherGroupX nz later, so
-// both find the shared planes in L2 (in plain tile order the x neighbour ran nt nz launches later,
-// hundreds of MB of staging traffic away).  A bijection of [0, tiles).
-constexpr int kGatherGroupX = 4;
-__device__ __forceinline__ int gather_order(const BinGeom& b, int t) {
-  const int bz = t % b.nz, u = t / b.nz;
-  const int bxg = u / (kGatherGroupX * b.nt), r = u - bxg * kGatherGroupX * b.nt;
-  const int left = b.nt - bxg * kGatherGroupX, gs = left < kGatherGroupX ? left : kGatherGroupX;
-  const int by = r / gs, bx = bxg * kGatherGroupX + (r - by * gs);
-  return (bx * b.nt + by) * b.nz + bz;
-}
-
 __device__ __forceinline__ GatherTile gather_tile_origin(const BinGeom& b, int tile) {
   const int bz = tile % b.nz, bxy = tile / b.nz;
   const int bx = bxy / b.nt, by = bxy - bx * b.nt;
@@ -490,7 +476,7 @@ __global__ void __launch_bounds__(kThreads) k_gather_tiles(ParticleGeom pg, BinG
                                                           float* s, float* v, const float* __restrict__ psi1,
                                                           const float* __restrict__ psi2, KickDrift kd, int* flags) {
   extern __shared__ __align__(16) float fsm[];
-  const int tile = gather_order(b, blockIdx.x);
+  const int tile = blockIdx.x;
   const unsigned e0 = off_p[tile], e1 = off_p[tile + 1];
   if (e0 == e1) return;                          // empty (uniform across the block)
   const GatherTile t = gather_tile_origin(b, tile);
