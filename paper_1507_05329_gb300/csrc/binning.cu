@@ -260,7 +260,8 @@ __global__ void __launch_bounds__(kThreads, COLA_DEPOSIT_MIN_BLOCKS) k_deposit_t
                                                            const unsigned* __restrict__ ent_p,
                                                            const unsigned* __restrict__ off_s,
                                                            const unsigned* __restrict__ ent_s,
-                                                           unsigned long long* rho) {
+                                                           unsigned long long* rho, float* delta_out, float scale,
+                                                           unsigned long long* mass_acc) {
   extern __shared__ unsigned long long acc[];
   const int lt = LT ? LT : b.lt, lz = LZ ? LZ : b.lz;
   const int nm = pg.n, T = 1 << lt, TZ = 1 << lz;
@@ -318,11 +319,26 @@ __global__ void __launch_bounds__(kThreads, COLA_DEPOSIT_MIN_BLOCKS) k_deposit_t
   }
   __syncthreads();
   // the tile owns its cells: plain, coalesced stores of T*T column segments of TZ cells
+  if (!delta_out) {
+    for (int i = threadIdx.x; i < cells; i += blockDim.x) {
+      const int col = i >> lz, z = i & (TZ - 1);
+      const int lx = col >> lt, ly = col & (T - 1);
+      rho[((long long)(x0 + lx) * nm + (y0 + ly)) * nm + z0 + z] = acc[i];
+    }
+    return;
+  }
+  // the density contrast instead of the fixed-point values, and the exact 128-bit total for the
+  // overflow check (every thread of the CTA's full warps reaches the warp reduction)
+  unsigned long long lo = 0ULL, hi = 0ULL;
   for (int i = threadIdx.x; i < cells; i += blockDim.x) {
     const int col = i >> lz, z = i & (TZ - 1);
     const int lx = col >> lt, ly = col & (T - 1);
-    rho[((long long)(x0 + lx) * nm + (y0 + ly)) * nm + z0 + z] = acc[i];
+    const unsigned long long v = acc[i];
+    lo += v;
+    hi += (lo < v);
+    delta_out[((long long)(x0 + lx) * nm + (y0 + ly)) * nm + z0 + z] = fixed_to_delta(v, scale);
   }
+  mass_accumulate(lo, hi, mass_acc);
 }
 
 // Tile-wise gather (+ kick and drift) over the primary entries of each tile, from a shared copy
@@ -642,12 +658,15 @@ int launch_binning(const ParticleGeom& pg, const BinGeom& b, const float* s, Bin
 }
 
 int launch_deposit_tiles(const ParticleGeom& pg, const BinGeom& b, const float* s, const BinBuffers& bb,
-                         unsigned long long* rho, cudaStream_t st) {
+                         unsigned long long* rho, cudaStream_t st, float* delta_out, float scale,
+                         unsigned long long* mass_acc) {
+  if (delta_out && !mass_acc) return COLA_ERR_INVALID;
   const FixedGeo fg = fixed_geo(pg.n, pg.r_fixed);
   with_instance(b, pg.n, [&](auto lt, auto lz, auto f32) {
     auto k = k_deposit_tiles<decltype(lt)::value, decltype(lz)::value, decltype(f32)::value>;
     smem_limit(k, 64 * 1024);
-    k<<<b.tiles, kThreads, bin_smem_bytes(b, pg.n), st>>>(pg, b, fg, s, bb.off_p, bb.ent_p, bb.off_s, bb.ent_s, rho);
+    k<<<b.tiles, kThreads, bin_smem_bytes(b, pg.n), st>>>(pg, b, fg, s, bb.off_p, bb.ent_p, bb.off_s, bb.ent_s, rho,
+                                                          delta_out, scale, mass_acc);
   });
   return check_launch("deposit_tiles");
 }

@@ -157,6 +157,20 @@ int forward_yz(cola_ctx* c, const unsigned long long* rho, bool check_mass) {
 }
 
 int deposit_and_forward_yz(cola_ctx* c, const float* s) {
+  if (c->binned) {
+    // the tile deposit writes the density contrast itself (half the bytes of the fixed-point mesh, and
+    // the z pass reads float rows); its exact 128-bit mass total feeds the overflow check
+    const Grid3& g = c->mesh;
+    const size_t n3 = (size_t)g.n * g.n * g.n;
+    const float scale = (float)((double)n3 / ((double)c->pg.npart * 4398046511104.0));   // N^3 / (n 2^42)
+    float* delta = reinterpret_cast<float*>(c->rho);
+    COLA_TRY(STAGED(kStBin, launch_binning(c->pg, c->bg, s, c->bb, c->stream)));
+    COLA_TRY(STAGED(kStDeposit, launch_deposit_tiles(c->pg, c->bg, s, c->bb, nullptr, c->stream, delta, scale,
+                                                     c->mass_acc)));
+    COLA_TRY(STAGED(kStFwdZ, launch_r2c_rows(c->mplan, g, kSrcFloat, delta, g.n, 1.0f, c->cbuf[2], c->stream)));
+    COLA_TRY(launch_mass_check(c->pg, nullptr, false, c->mass_acc, c->flags, c->stream));
+    return STAGED(kStFwdY, launch_pencils(c->mplan, g, 1, -1, c->cbuf[2], c->stream));
+  }
   COLA_TRY(deposit_mesh(c, s, c->rho));
   return forward_yz(c, c->rho, true);
 }

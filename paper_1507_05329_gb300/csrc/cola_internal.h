@@ -189,6 +189,15 @@ __device__ __forceinline__ void cell_frac(int q, float s, const FixedGeo& f, int
 #endif
 
 #ifdef __CUDACC__
+// Density contrast of one fixed-point mesh cell, delta = rho scale - 1 (scale = N^3 / (n 2^42)), the
+// same float in every kernel that forms it (the tile deposit, the R2C passes, the generic FFT): rho
+// is converted as hi 2^32 + lo with two exact-range 32-bit conversions and one fused multiply-add
+// (FP32 units only; a 64-bit integer conversion runs on GB300's few FP64 units), then one more FMA.
+__device__ __forceinline__ float fixed_to_delta(unsigned long long v, float scale) {
+  const float f = __fmaf_rn(__uint2float_rn((unsigned)(v >> 32)), 4294967296.0f, __uint2float_rn((unsigned)v));
+  return __fmaf_rn(f, scale, -1.0f);
+}
+
 // Adds a thread's 128-bit partial (lo, hi) to the global accumulator acc[0..1] (exact, any order).
 // Called by every thread of full warps.
 __device__ __forceinline__ void mass_accumulate(unsigned long long lo, unsigned long long hi, unsigned long long* acc) {
@@ -232,8 +241,12 @@ bool bin_geometry(int nmesh, int np, BinGeom* b);
 size_t bin_smem_bytes(const BinGeom& b, int nmesh);
 bool tile_gather_pays(const BinGeom& b, long long npart);   // else gather in lattice order
 int launch_binning(const ParticleGeom& pg, const BinGeom& b, const float* s, BinBuffers& bb, cudaStream_t st);
+// delta_out == nullptr: writes the fixed-point mesh rho.  Else writes the density contrast
+// fixed_to_delta(rho, scale) as dense float rows to delta_out (rho is not written) and adds the exact
+// 128-bit total of the mesh to mass_acc (for launch_mass_check).
 int launch_deposit_tiles(const ParticleGeom& pg, const BinGeom& b, const float* s, const BinBuffers& bb,
-                         unsigned long long* rho, cudaStream_t st);
+                         unsigned long long* rho, cudaStream_t st, float* delta_out = nullptr, float scale = 0.0f,
+                         unsigned long long* mass_acc = nullptr);
 int launch_gather_tiles(const ParticleGeom& pg, const BinGeom& b, const BinBuffers& bb, const float* const f[3],
                         long long rs, const float* s_in, float* force_out, float* s, float* v, const float* psi1,
                         const float* psi2, const KickDrift* kd, int* flags, cudaStream_t st,

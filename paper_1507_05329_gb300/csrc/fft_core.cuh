@@ -657,13 +657,13 @@ struct RowPairSrc {   // complex (row 2w, row 2w+1) at column j of real rows
       const unsigned long long* s = static_cast<const unsigned long long*>(src);
       if (ra < nrows) {
         const unsigned long long va = s[ra * rs + j];
-        a = __ull2float_rn(va) * scale - 1.0f;
+        a = fixed_to_delta(va, scale);
         mlo += va;
         mhi += (mlo < va);
       }
       if (ra + 1 < nrows) {
         const unsigned long long vb = s[(ra + 1) * rs + j];
-        b = __ull2float_rn(vb) * scale - 1.0f;
+        b = fixed_to_delta(vb, scale);
         mlo += vb;
         mhi += (mlo < vb);
       }

@@ -21,13 +21,13 @@ __global__ void __launch_bounds__(kMaxThreads, 2) k_r2c_rows(FftDev p, int lw, c
       const unsigned long long* s = static_cast<const unsigned long long*>(src);
       if (ra < nrows) {
         const unsigned long long va = s[ra * src_rs + j];
-        a = __ull2float_rn(va) * scale - 1.0f;
+        a = fixed_to_delta(va, scale);
         mlo += va;
         mhi += (mlo < va);
       }
       if (ra + 1 < nrows) {
         const unsigned long long vb = s[(ra + 1) * src_rs + j];
-        b = __ull2float_rn(vb) * scale - 1.0f;
+        b = fixed_to_delta(vb, scale);
         mlo += vb;
         mhi += (mlo < vb);
       }
