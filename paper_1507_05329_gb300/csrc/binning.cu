@@ -338,7 +338,32 @@ __global__ void __launch_bounds__(kThreads, COLA_DEPOSIT_MIN_BLOCKS) k_deposit_t
     hi += (lo < v);
     delta_out[((long long)(x0 + lx) * nm + (y0 + ly)) * nm + z0 + z] = fixed_to_delta(v, scale);
   }
-  mass_accumulate(lo, hi, mass_acc);
+  // the CTA's total (warp shuffles, then the warps' partials in shared memory) and one slot update
+  for (int off = 16; off > 0; off >>= 1) {
+    const unsigned long long olo = __shfl_down_sync(0xffffffffu, lo, off);
+    const unsigned long long ohi = __shfl_down_sync(0xffffffffu, hi, off);
+    lo += olo;
+    hi += ohi + (lo < olo);
+  }
+  __shared__ unsigned long long wpart[2 * (kThreads / 32)];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+    wpart[2 * warp] = lo;
+    wpart[2 * warp + 1] = hi;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long tlo = 0ULL, thi = 0ULL;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      tlo += wpart[2 * w];
+      thi += wpart[2 * w + 1] + (tlo < wpart[2 * w]);
+    }
+    if (tlo | thi) {
+      unsigned long long* slot = mass_slot(mass_acc);
+      const unsigned long long old = atomicAdd(slot, tlo);
+      atomicAdd(slot + 1, thi + (old + tlo < old));
+    }
+  }
 }
 
 // Tile-wise gather (+ kick and drift) over the primary entries of each tile, from a shared copy

@@ -379,10 +379,10 @@ extern "C" int cola_create(const cola_params* params, void* stream, cola_ctx** o
                         "cudaMalloc")) != COLA_OK ||
       (st = cuda_status(cudaMalloc(&c->pk_geom, 2 * kPkMaxBins * sizeof(double)), "cudaMalloc")) != COLA_OK ||
       (st = cuda_status(cudaMalloc(&c->flags, sizeof(int)), "cudaMalloc")) != COLA_OK ||
-      (st = cuda_status(cudaMalloc(&c->mass_acc, 2 * sizeof(unsigned long long)), "cudaMalloc")) != COLA_OK)
+      (st = cuda_status(cudaMalloc(&c->mass_acc, 2 * kMassSlots * sizeof(unsigned long long)), "cudaMalloc")) != COLA_OK)
     return fail(st);
   cudaMemset(c->flags, 0, sizeof(int));
-  cudaMemset(c->mass_acc, 0, 2 * sizeof(unsigned long long));
+  cudaMemset(c->mass_acc, 0, 2 * kMassSlots * sizeof(unsigned long long));
   // tile binning buffers: 6 per-tile arrays, n primary entries and up to 7n spill entries
   if (bin_geometry(params->nmesh, params->np, &c->bg)) {
     const size_t tiles = (size_t)c->bg.tiles + 1;

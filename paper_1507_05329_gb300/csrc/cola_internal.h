@@ -198,7 +198,14 @@ __device__ __forceinline__ float fixed_to_delta(unsigned long long v, float scal
   return __fmaf_rn(f, scale, -1.0f);
 }
 
-// Adds a thread's 128-bit partial (lo, hi) to the global accumulator acc[0..1] (exact, any order).
+// The 128-bit mass accumulator is kMassSlots (lo, hi) pairs, one chosen per CTA, so that the atomics of
+// many CTAs do not all land on one address; launch_mass_check sums the slots.
+constexpr int kMassSlots = 128;
+__device__ __forceinline__ unsigned long long* mass_slot(unsigned long long* acc) {
+  return acc + 2 * (blockIdx.x & (kMassSlots - 1));
+}
+
+// Adds a thread's 128-bit partial (lo, hi) to the accumulator pair acc[0..1] (exact, any order).
 // Called by every thread of full warps.
 __device__ __forceinline__ void mass_accumulate(unsigned long long lo, unsigned long long hi, unsigned long long* acc) {
   for (int off = 16; off > 0; off >>= 1) {

@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) k_r2c_rows(FftDev p, int lw, c
     }
     sm[saddr(j, w, lw)] = make_float2(a, b);
   }
-  if (SRC == kSrcFixedPoint && mass_acc) mass_accumulate(mlo, mhi, mass_acc);
+  if (SRC == kSrcFixedPoint && mass_acc) mass_accumulate(mlo, mhi, mass_slot(mass_acc));
   __syncthreads();
   const float2* res = fft_smem<-1>(sm, sm + tile_elems(n, lw), p, lw, tid, nt);
   const int nh = n / 2;

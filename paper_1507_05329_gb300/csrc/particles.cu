@@ -148,9 +148,14 @@ __global__ void __launch_bounds__(kRowThreads) k_gather(ParticleGeom pg, const f
 __global__ void k_mass_check(const unsigned long long* __restrict__ acc, unsigned long long expect_lo,
                              unsigned long long expect_hi, unsigned long long* acc_reset, int* flags) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
-    if (acc[0] != expect_lo || acc[1] != expect_hi) atomicOr(flags, 1);
-    acc_reset[0] = 0ULL;
-    acc_reset[1] = 0ULL;
+    unsigned long long lo = 0ULL, hi = 0ULL;
+    for (int k = 0; k < kMassSlots; ++k) {
+      const unsigned long long l = acc[2 * k];
+      lo += l;
+      hi += acc[2 * k + 1] + (lo < l);
+    }
+    if (lo != expect_lo || hi != expect_hi) atomicOr(flags, 1);
+    for (int k = 0; k < 2 * kMassSlots; ++k) acc_reset[k] = 0ULL;
   }
 }
 
@@ -161,7 +166,7 @@ __global__ void k_mesh_sum(const unsigned long long* __restrict__ rho, long long
     lo += v;
     hi += (lo < v);
   }
-  mass_accumulate(lo, hi, acc);
+  mass_accumulate(lo, hi, mass_slot(acc));
 }
 
 // ---- 2LPT helpers on the lattice grid (side n = np, half spectrum rows of pc) --------------
