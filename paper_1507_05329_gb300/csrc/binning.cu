@@ -261,7 +261,7 @@ __global__ void __launch_bounds__(kThreads, COLA_DEPOSIT_MIN_BLOCKS) k_deposit_t
                                                            const unsigned* __restrict__ off_s,
                                                            const unsigned* __restrict__ ent_s,
                                                            unsigned long long* rho, float* delta_out, float scale,
-                                                           unsigned long long* mass_acc) {
+                                                           unsigned long long* tile_mass) {
   extern __shared__ unsigned long long acc[];
   const int lt = LT ? LT : b.lt, lz = LZ ? LZ : b.lz;
   const int nm = pg.n, T = 1 << lt, TZ = 1 << lz;
@@ -358,11 +358,8 @@ __global__ void __launch_bounds__(kThreads, COLA_DEPOSIT_MIN_BLOCKS) k_deposit_t
       tlo += wpart[2 * w];
       thi += wpart[2 * w + 1] + (tlo < wpart[2 * w]);
     }
-    if (tlo | thi) {
-      unsigned long long* slot = mass_slot(mass_acc);
-      const unsigned long long old = atomicAdd(slot, tlo);
-      atomicAdd(slot + 1, thi + (old + tlo < old));
-    }
+    tile_mass[2 * blockIdx.x] = tlo;   // one pair per tile, no atomics; launch_mass_reduce sums them
+    tile_mass[2 * blockIdx.x + 1] = thi;
   }
 }
 
@@ -684,14 +681,14 @@ int launch_binning(const ParticleGeom& pg, const BinGeom& b, const float* s, Bin
 
 int launch_deposit_tiles(const ParticleGeom& pg, const BinGeom& b, const float* s, const BinBuffers& bb,
                          unsigned long long* rho, cudaStream_t st, float* delta_out, float scale,
-                         unsigned long long* mass_acc) {
-  if (delta_out && !mass_acc) return COLA_ERR_INVALID;
+                         unsigned long long* tile_mass) {
+  if (delta_out && !tile_mass) return COLA_ERR_INVALID;
   const FixedGeo fg = fixed_geo(pg.n, pg.r_fixed);
   with_instance(b, pg.n, [&](auto lt, auto lz, auto f32) {
     auto k = k_deposit_tiles<decltype(lt)::value, decltype(lz)::value, decltype(f32)::value>;
     smem_limit(k, 64 * 1024);
     k<<<b.tiles, kThreads, bin_smem_bytes(b, pg.n), st>>>(pg, b, fg, s, bb.off_p, bb.ent_p, bb.off_s, bb.ent_s, rho,
-                                                          delta_out, scale, mass_acc);
+                                                          delta_out, scale, tile_mass);
   });
   return check_launch("deposit_tiles");
 }

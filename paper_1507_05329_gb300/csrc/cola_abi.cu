@@ -166,8 +166,9 @@ int deposit_and_forward_yz(cola_ctx* c, const float* s) {
     float* delta = reinterpret_cast<float*>(c->rho);
     COLA_TRY(STAGED(kStBin, launch_binning(c->pg, c->bg, s, c->bb, c->stream)));
     COLA_TRY(STAGED(kStDeposit, launch_deposit_tiles(c->pg, c->bg, s, c->bb, nullptr, c->stream, delta, scale,
-                                                     c->mass_acc)));
+                                                     c->tile_mass)));
     COLA_TRY(STAGED(kStFwdZ, launch_r2c_rows(c->mplan, g, kSrcFloat, delta, g.n, 1.0f, c->cbuf[2], c->stream)));
+    COLA_TRY(launch_mass_reduce(c->tile_mass, c->bg.tiles, c->mass_acc, c->stream));
     COLA_TRY(launch_mass_check(c->pg, nullptr, false, c->mass_acc, c->flags, c->stream));
     return STAGED(kStFwdY, launch_pencils(c->mplan, g, 1, -1, c->cbuf[2], c->stream));
   }
@@ -388,7 +389,8 @@ extern "C" int cola_create(const cola_params* params, void* stream, cola_ctx** o
     const size_t tiles = (size_t)c->bg.tiles + 1;
     const size_t nseg = (tiles + 4095) / 4096 + 1;
     const size_t bytes = 6 * align256(tiles * sizeof(unsigned)) + align256((size_t)c->pg.npart * 4) +
-                         align256((size_t)c->pg.npart * 28) + align256(2 * nseg * sizeof(unsigned));
+                         align256((size_t)c->pg.npart * 28) + align256(2 * nseg * sizeof(unsigned)) +
+                         align256(tiles * 2 * sizeof(unsigned long long));
     if ((st = cuda_status(cudaMalloc(&c->bin_mem, bytes), "cudaMalloc bins")) != COLA_OK) return fail(st);
     char* q = static_cast<char*>(c->bin_mem);
     unsigned** arr[6] = {&c->bb.cnt_p, &c->bb.cnt_s, &c->bb.off_p, &c->bb.off_s, &c->bb.cur_p, &c->bb.cur_s};
@@ -401,6 +403,8 @@ extern "C" int cola_create(const cola_params* params, void* stream, cola_ctx** o
     c->bb.ent_s = reinterpret_cast<unsigned*>(q);
     q += align256((size_t)c->pg.npart * 28);
     c->bb.seg = reinterpret_cast<unsigned*>(q);
+    q += align256(2 * nseg * sizeof(unsigned));
+    c->tile_mass = reinterpret_cast<unsigned long long*>(q);
     c->binned = true;
     c->tile_gather = tile_gather_pays(c->bg, c->pg.npart);
   }

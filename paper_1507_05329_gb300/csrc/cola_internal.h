@@ -126,6 +126,8 @@ int launch_deposit(const ParticleGeom& pg, const float* s, unsigned long long* r
 // summing rho here when sum_mesh) differs from n 2^42, i.e. if some cell wrapped; resets acc.
 int launch_mass_check(const ParticleGeom& pg, const unsigned long long* rho, bool sum_mesh, unsigned long long* acc,
                       int* flags, cudaStream_t st);
+// Adds the 128-bit sum of m (lo, hi) pairs to the accumulator acc (kMassSlots pairs).
+int launch_mass_reduce(const unsigned long long* pairs, long long m, unsigned long long* acc, cudaStream_t st);
 
 // Fixed-point particle coordinates shared by the deposit, the gathers, the adjoint and FoF: a
 // particle at lattice index q (per axis) and displacement s (mesh cells) sits at
@@ -249,11 +251,11 @@ size_t bin_smem_bytes(const BinGeom& b, int nmesh);
 bool tile_gather_pays(const BinGeom& b, long long npart);   // else gather in lattice order
 int launch_binning(const ParticleGeom& pg, const BinGeom& b, const float* s, BinBuffers& bb, cudaStream_t st);
 // delta_out == nullptr: writes the fixed-point mesh rho.  Else writes the density contrast
-// fixed_to_delta(rho, scale) as dense float rows to delta_out (rho is not written) and adds the exact
-// 128-bit total of the mesh to mass_acc (for launch_mass_check).
+// fixed_to_delta(rho, scale) as dense float rows to delta_out (rho is not written) and each tile's
+// exact 128-bit total to tile_mass[2 tile .. 2 tile + 1] (for launch_mass_reduce).
 int launch_deposit_tiles(const ParticleGeom& pg, const BinGeom& b, const float* s, const BinBuffers& bb,
                          unsigned long long* rho, cudaStream_t st, float* delta_out = nullptr, float scale = 0.0f,
-                         unsigned long long* mass_acc = nullptr);
+                         unsigned long long* tile_mass = nullptr);
 int launch_gather_tiles(const ParticleGeom& pg, const BinGeom& b, const BinBuffers& bb, const float* const f[3],
                         long long rs, const float* s_in, float* force_out, float* s, float* v, const float* psi1,
                         const float* psi2, const KickDrift* kd, int* flags, cudaStream_t st,
@@ -371,6 +373,7 @@ struct cola_ctx {
   bool spec_saved = false;                // the last force evaluation left delta(k) in the rho buffer
   int* flags = nullptr;                   // sticky device error flags
   unsigned long long* mass_acc = nullptr; // 128-bit total of the fixed-point mesh (overflow check)
+  unsigned long long* tile_mass = nullptr;  // [tiles][2] 128-bit totals of the tile deposit
   bool binned = false;                    // tile-wise deposit (else direct atomics)
   bool tile_gather = false;               // tile-wise gather from shared memory (else lattice order)
   bool gather_pipe = false;               // ... by persistent CTAs that stage the next tile meanwhile

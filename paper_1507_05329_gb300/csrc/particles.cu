@@ -501,6 +501,22 @@ int launch_deposit(const ParticleGeom& pg, const float* s, unsigned long long* r
   return check_launch("deposit");
 }
 
+// 128-bit sum of m (lo, hi) pairs into the accumulator slots
+__global__ void k_mass_reduce(const unsigned long long* __restrict__ pairs, long long m, unsigned long long* acc) {
+  unsigned long long lo = 0, hi = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < m; i += (long long)gridDim.x * blockDim.x) {
+    const unsigned long long l = pairs[2 * i];
+    lo += l;
+    hi += pairs[2 * i + 1] + (lo < l);
+  }
+  mass_accumulate(lo, hi, mass_slot(acc));
+}
+
+int launch_mass_reduce(const unsigned long long* pairs, long long m, unsigned long long* acc, cudaStream_t st) {
+  k_mass_reduce<<<grid_for(m, 256), 256, 0, st>>>(pairs, m, acc);
+  return check_launch("mass_reduce");
+}
+
 int launch_mass_check(const ParticleGeom& pg, const unsigned long long* rho, bool sum_mesh, unsigned long long* acc,
                       int* flags, cudaStream_t st) {
   if (sum_mesh) {
