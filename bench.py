@@ -77,13 +77,17 @@ def whole_job_rate(world: int, particles: int, nstep: int, ms: float) -> float:
 
 
 # ---- algorithmic bytes per launch of each stage (mesh N, particles n) ---------------------------
-def stage_bytes(n_mesh: int, n_part: int) -> dict:
+def stage_bytes(n_mesh: int, n_part: int, binned: bool = True) -> dict:
+    """Bytes each stage must move once.  The tile (binned) deposit sums the exact fixed-point mesh in
+    shared memory and writes the float density contrast (4 B per cell), which the z pass reads; the
+    direct deposit writes and the z pass reads the 8-byte fixed-point mesh."""
     nc = n_mesh // 2 + 1
     cplx = 8.0 * n_mesh * n_mesh * nc          # one complex half-spectrum field
     real = 4.0 * n_mesh ** 3                   # one real field
+    mesh = (4.0 if binned else 8.0) * n_mesh ** 3
     return {
-        "deposit": 12.0 * n_part + 8.0 * n_mesh ** 3,
-        "fwd_z_r2c": 8.0 * n_mesh ** 3 + cplx,
+        "deposit": 12.0 * n_part + mesh,
+        "fwd_z_r2c": mesh + cplx,
         "fwd_y": 2 * cplx,
         "green_x": cplx + 3 * cplx,
         "inv_y": 2 * cplx,
@@ -561,6 +565,7 @@ def run_ours(args):
         ctx.run(wn, args.nbins, out=out)
         ctx.sync()
 
+    ctx_schedule = ctx.schedule
     sampler = ClockSampler(local)
     ctx.profile(True)
     barrier()
@@ -591,7 +596,7 @@ def run_ours(args):
         dist.all_gather_object(rank_devices, me)
 
     # roofline of the dominant PM-step kernel
-    sb = stage_bytes(p.nmesh, n)
+    sb = stage_bytes(p.nmesh, n, binned=bool(ctx_schedule & binding.SCHED_BINNED_DEPOSIT))
     stages = {k: {"ms_total": v[0], "launches": v[1]} for k, v in prof.items()}
     pm_stages = [k for k in sb if prof[k][1] > 0]
     dom = max(pm_stages, key=lambda k: prof[k][0])

@@ -29,7 +29,7 @@ namespace {
 
 constexpr int kThreads = 256;
 #ifndef COLA_DEPOSIT_MIN_BLOCKS
-#define COLA_DEPOSIT_MIN_BLOCKS 6   // resident deposit CTAs per SM the register budget is sized for
+#define COLA_DEPOSIT_MIN_BLOCKS 8   // resident deposit CTAs per SM the register budget is sized for
 #endif
 
 int check_launch(const char* what) {
