@@ -102,12 +102,36 @@ __device__ __forceinline__ void tile_keys(const BinGeom& b, int cx, int cy, int 
   }
 }
 
-template <bool SCATTER, int LT, int LZ, bool F32>
-__global__ void __launch_bounds__(kThreads) k_bin(ParticleGeom pg, BinGeom b, FixedGeo fg, const float* __restrict__ s,
-                                                  unsigned* cnt_p, unsigned* cnt_s, unsigned* ent_p, unsigned* ent_s) {
+// Spill keys of a particle from its primary tile key and its three upper-face flags (the keys
+// tile_keys gives, without the particle's position).
+__device__ __forceinline__ void keys_from_record(const BinGeom& b, unsigned key, unsigned flags, int* k) {
+  const int bz = (int)(key % (unsigned)b.nz), bxy = (int)(key / (unsigned)b.nz);
+  const int bx = bxy / b.nt, by = bxy - bx * b.nt;
+  const bool sx = flags & 1u, sy = flags & 2u, sz = flags & 4u;
+  const int bxs[2] = {bx, bx + 1 == b.nt ? 0 : bx + 1};
+  const int bys[2] = {by, by + 1 == b.nt ? 0 : by + 1};
+  const int bzs[2] = {bz, bz + 1 == b.nz ? 0 : bz + 1};
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const int dx = c >> 2, dy = (c >> 1) & 1, dz = c & 1;
+    const bool ok = (!dx || sx) && (!dy || sy) && (!dz || sz);
+    k[c] = ok ? (bxs[dx] * b.nt + bys[dy]) * b.nz + bzs[dz] : -1;
+  }
+}
+
+// Count pass: per-tile primary and spill counts; every particle's rank within its primary tile (the
+// aggregated atomic's return) is recorded with its tile key and upper-face flags, so that the scatter
+// pass needs neither the positions nor atomics for the primary entries.
+//   rec[id] = rank << 32 | flags << 26 | key   (key < 2^26 tiles, flags: x, y, z upper face)
+template <int LT, int LZ, bool F32>
+__global__ void __launch_bounds__(kThreads) k_bin_count(ParticleGeom pg, BinGeom b, FixedGeo fg,
+                                                        const float* __restrict__ s, unsigned* cnt_p, unsigned* cnt_s,
+                                                        unsigned long long* __restrict__ rec) {
   const long long n = pg.npart;
   const int np = pg.np;
   const long long nrows = (long long)np * np;
+  const int lt = LT ? LT : b.lt, lz = LZ ? LZ : b.lz;
+  const int m = (1 << lt) - 1, mz = (1 << lz) - 1;
   // the block walks (row, chunk) pairs; the positions of the next pair are loaded before this
   // pair's atomics, so the two latencies overlap
   const int nch = (np + (int)blockDim.x - 1) / (int)blockDim.x;
@@ -138,32 +162,56 @@ __global__ void __launch_bounds__(kThreads) k_bin(ParticleGeom pg, BinGeom b, Fi
     const int qz = ch * (int)blockDim.x + (int)threadIdx.x;
     const bool live = qz < np;
     int k[8] = {-1, -1, -1, -1, -1, -1, -1, -1};
+    unsigned flags = 0;
     if (live) {
       int cx, cy, cz, f;
       cell_frac<F32>(qx, p0, fg, &cx, &f);
       cell_frac<F32>(qy, p1, fg, &cy, &f);
       cell_frac<F32>(qz, p2, fg, &cz, &f);
       tile_keys<LT, LZ>(b, cx, cy, cz, k);
+      flags = (b.nt > 1 && (cx & m) == m ? 1u : 0u) | (b.nt > 1 && (cy & m) == m ? 2u : 0u) |
+              (b.nz > 1 && (cz & mz) == mz ? 4u : 0u);
     }
-    const unsigned packed = pack_q(qx, qy, qz);
     if (__any_sync(__activemask(), live)) {
       // primary keys are shared by runs of lanes: one aggregated atomic per run
-      const unsigned slot = agg_inc(cnt_p, k[0], SCATTER);
-      if (SCATTER && k[0] >= 0) ent_p[slot] = packed;
+      const unsigned rank = agg_inc(cnt_p, k[0], true);
+      if (live) rec[row * np + qz] = ((unsigned long long)rank << 32) | ((unsigned long long)flags << 26) | (unsigned)k[0];
     }
-    // spill keys are sparse: one atomic per entry
+    // spill keys are sparse: one atomic per entry (its result unused)
 #pragma unroll
-    for (int e = 1; e < 8; ++e) {
-      if (k[e] >= 0) {
-        const unsigned sl = atomicAdd(cnt_s + k[e], 1u);
-        if (SCATTER) ent_s[sl] = packed;
-      }
-    }
+    for (int e = 1; e < 8; ++e)
+      if (k[e] >= 0) atomicAdd(cnt_s + k[e], 1u);
     row = nrow;
     ch = nchk;
     p0 = n0;
     p1 = n1;
     p2 = n2;
+  }
+}
+
+// Scatter pass from the records: primary entries straight to offset + rank, spill entries through
+// the spill cursors.
+__global__ void __launch_bounds__(kThreads) k_bin_scatter(ParticleGeom pg, BinGeom b,
+                                                          const unsigned long long* __restrict__ rec,
+                                                          const unsigned* __restrict__ off_p, unsigned* cur_s,
+                                                          unsigned* ent_p, unsigned* ent_s) {
+  const int np = pg.np;
+  const long long nrows = (long long)np * np;
+  for (long long row = blockIdx.x; row < nrows; row += gridDim.x) {
+    const int qx = (int)(row / np), qy = (int)(row - (long long)qx * np);
+    for (int qz = threadIdx.x; qz < np; qz += blockDim.x) {
+      const unsigned long long r = __ldcs(rec + row * np + qz);
+      const unsigned key = (unsigned)r & ((1u << 26) - 1u), flags = ((unsigned)r >> 26) & 7u;
+      const unsigned packed = pack_q(qx, qy, qz);
+      ent_p[off_p[key] + (unsigned)(r >> 32)] = packed;
+      if (flags) {
+        int k[8];
+        keys_from_record(b, key, flags, k);
+#pragma unroll
+        for (int e = 1; e < 8; ++e)
+          if (k[e] >= 0) ent_s[atomicAdd(cur_s + k[e], 1u)] = packed;
+      }
+    }
   }
 }
 
@@ -666,8 +714,8 @@ int launch_binning(const ParticleGeom& pg, const BinGeom& b, const float* s, Bin
       cudaMemsetAsync(bb.cnt_s, 0, (size_t)b.tiles * sizeof(unsigned), st) != cudaSuccess)
     return COLA_ERR_CUDA;
   with_instance(b, pg.n, [&](auto lt, auto lz, auto f32) {
-    k_bin<false, decltype(lt)::value, decltype(lz)::value, decltype(f32)::value>
-        <<<grid, th, 0, st>>>(pg, b, fg, s, bb.cnt_p, bb.cnt_s, nullptr, nullptr);
+    k_bin_count<decltype(lt)::value, decltype(lz)::value, decltype(f32)::value>
+        <<<grid, th, 0, st>>>(pg, b, fg, s, bb.cnt_p, bb.cnt_s, bb.rec);
   });
   int e = check_launch("bin_count");
   if (e != COLA_OK) return e;
@@ -677,10 +725,7 @@ int launch_binning(const ParticleGeom& pg, const BinGeom& b, const float* s, Bin
   k_scan_apply<<<dim3(nseg, 2), kScanThreads, 0, st>>>(bb.cnt_p, bb.cnt_s, b.tiles, bb.seg, bb.off_p, bb.off_s,
                                                        bb.cur_p, bb.cur_s);
   if ((e = check_launch("bin_scan")) != COLA_OK) return e;
-  with_instance(b, pg.n, [&](auto lt, auto lz, auto f32) {
-    k_bin<true, decltype(lt)::value, decltype(lz)::value, decltype(f32)::value>
-        <<<grid, th, 0, st>>>(pg, b, fg, s, bb.cur_p, bb.cur_s, bb.ent_p, bb.ent_s);
-  });
+  k_bin_scatter<<<grid, th, 0, st>>>(pg, b, bb.rec, bb.off_p, bb.cur_s, bb.ent_p, bb.ent_s);
   return check_launch("bin_scatter");
 }
 

@@ -390,7 +390,7 @@ extern "C" int cola_create(const cola_params* params, void* stream, cola_ctx** o
     const size_t nseg = (tiles + 4095) / 4096 + 1;
     const size_t bytes = 6 * align256(tiles * sizeof(unsigned)) + align256((size_t)c->pg.npart * 4) +
                          align256((size_t)c->pg.npart * 28) + align256(2 * nseg * sizeof(unsigned)) +
-                         align256(tiles * 2 * sizeof(unsigned long long));
+                         align256(tiles * 2 * sizeof(unsigned long long)) + align256((size_t)c->pg.npart * 8);
     if ((st = cuda_status(cudaMalloc(&c->bin_mem, bytes), "cudaMalloc bins")) != COLA_OK) return fail(st);
     char* q = static_cast<char*>(c->bin_mem);
     unsigned** arr[6] = {&c->bb.cnt_p, &c->bb.cnt_s, &c->bb.off_p, &c->bb.off_s, &c->bb.cur_p, &c->bb.cur_s};
@@ -405,6 +405,8 @@ extern "C" int cola_create(const cola_params* params, void* stream, cola_ctx** o
     c->bb.seg = reinterpret_cast<unsigned*>(q);
     q += align256(2 * nseg * sizeof(unsigned));
     c->tile_mass = reinterpret_cast<unsigned long long*>(q);
+    q += align256(tiles * 2 * sizeof(unsigned long long));
+    c->bb.rec = reinterpret_cast<unsigned long long*>(q);
     c->binned = true;
     c->tile_gather = tile_gather_pays(c->bg, c->pg.npart);
   }

@@ -245,6 +245,7 @@ struct BinBuffers {
   unsigned *cur_p = nullptr, *cur_s = nullptr;   // scatter cursors
   unsigned *ent_p = nullptr, *ent_s = nullptr;   // packed lattice coordinates (n primary, up to 7n spill)
   unsigned* seg = nullptr;                        // scan segment sums (2 lists)
+  unsigned long long* rec = nullptr;              // [n] rank in the primary tile << 32 | flags << 26 | tile
 };
 bool bin_geometry(int nmesh, int np, BinGeom* b);
 size_t bin_smem_bytes(const BinGeom& b, int nmesh);
