@@ -566,6 +566,9 @@ def run_ours(args):
         ctx.sync()
 
     ctx_schedule = ctx.schedule
+    # kernels per realisation, counted from a captured (unexecuted) graph of the same cola_run call
+    kernels_per_run = ctx.run_kernel_count(wn, args.nbins, out=out)
+    ctx.sync()
     sampler = ClockSampler(local)
     ctx.profile(True)
     barrier()
@@ -621,7 +624,7 @@ def run_ours(args):
             a = prof[k][0] / prof[k][1]
             per_stage[k] = {"avg_ms": round(a, 4), "launches": prof[k][1],
                             "GBps": round(sb[k] / (a / 1e3) / 1e9, 1), "frac": round(sb[k] / (a / 1e3) / 1e9 / peak, 3)}
-    launches = sum(v[1] for k, v in prof.items() if k != "clear")
+    launches = kernels_per_run * args.steps
     if prof.get("bin", (0, 0))[1]:
         per_stage["bin"] = {"avg_ms": round(prof["bin"][0] / prof["bin"][1], 4), "launches": prof["bin"][1],
                             "note": "particle binning by mesh tiles (implementation overhead, not algorithmic bytes)"}

@@ -161,6 +161,15 @@ int cola_step(cola_ctx* ctx, int i, float* s, float* v, const float* psi1, const
 int cola_run(cola_ctx* ctx, const float* white_noise, float* s, float* v, float* psi1,
              float* psi2, double* pk, int nbins);
 
+/* The number of kernels one cola_run call with these arguments launches (written to *kernels): the
+ * call is captured into a CUDA graph on a private stream, its kernel nodes are counted and the
+ * graph is destroyed unexecuted, so no buffer is touched.  Memset and copy nodes are not kernels.
+ * Call it after one plain cola_run with the same nbins (the capture cannot upload new P(k) bin
+ * edges or set first-use kernel attributes).  Profiling counters are left as they were.
+ * COLA_ERR_INVALID for a NULL kernels or an nbins different from the last P(k) call's. */
+int cola_run_kernel_count(cola_ctx* ctx, const float* white_noise, float* s, float* v, float* psi1,
+                          float* psi2, double* pk, int nbins, long long* kernels);
+
 /* S6 — matter power spectrum of the particles at displacement s (§3.3): CIC deposit, FFT, the
  * modes {kz>0} U {kz=0,ky>0} U {kz=0,ky=0,kx>0}, nbins log-spaced bins between 2 pi/L and
  * pi N/L decided on the integer |m|^2, P = V |delta_k|^2 / N^6 averaged per bin.

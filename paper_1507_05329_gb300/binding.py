@@ -78,6 +78,7 @@ SIGNATURES = {
     "cola_pm_force_of_mesh": ([_VP, _VP, _D, _VP, ctypes.c_longlong, _VP], _I),
     "cola_step": ([_VP, _I, _VP, _VP, _VP, _VP], _I),
     "cola_run": ([_VP, _VP, _VP, _VP, _VP, _VP, _VP, _I], _I),
+    "cola_run_kernel_count": ([_VP, _VP, _VP, _VP, _VP, _VP, _VP, _I, ctypes.POINTER(ctypes.c_longlong)], _I),
     "cola_power_spectrum": ([_VP, _VP, _VP, _I], _I),
     "cola_profile_enable": ([_VP, _I], _I),
     "cola_profile_read": ([_VP, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong), _I], _I),
@@ -384,6 +385,22 @@ class Context:
                                  self._particles(p2), _ptr(pk, self.torch) if with_pk else None, int(nbins)),
                "cola_run")
         return dict(s=s, v=v, psi1=p1, psi2=p2, pk=pk)
+
+    def run_kernel_count(self, white_noise=None, nbins: int = 64, with_pk: bool = True, out: dict | None = None) -> int:
+        """Kernels one ``run`` with these arguments launches (cola_run_kernel_count: captured, counted,
+        not executed).  Call after one ``run`` with the same nbins."""
+        wn = self._noise(white_noise)
+        if out is None:
+            s, v, p1, p2 = (self.empty_particles() for _ in range(4))
+            pk = self.torch.empty((3, nbins), dtype=self.torch.float64, device=self.device) if with_pk else None
+        else:
+            s, v, p1, p2, pk = out["s"], out["v"], out["psi1"], out["psi2"], out.get("pk")
+        k = ctypes.c_longlong()
+        _check(self.lib.cola_run_kernel_count(self._ptr, wn, self._particles(s), self._particles(v),
+                                              self._particles(p1), self._particles(p2),
+                                              _ptr(pk, self.torch) if with_pk else None, int(nbins),
+                                              ctypes.byref(k)), "cola_run_kernel_count")
+        return int(k.value)
 
     # -- reverse mode ----------------------------------------------------------------------
     def run_checkpointed(self, white_noise=None):

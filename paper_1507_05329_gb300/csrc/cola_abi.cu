@@ -12,6 +12,7 @@
 //   S6 power spectrum ...... §3.3
 #include "cola_internal.h"
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -628,6 +629,44 @@ extern "C" int cola_run(cola_ctx* c, const float* wn, float* s, float* v, float*
     else COLA_TRY(cola_power_spectrum(c, s, pk, nbins));
   }
   return COLA_OK;
+}
+
+extern "C" int cola_run_kernel_count(cola_ctx* c, const float* wn, float* s, float* v, float* psi1, float* psi2,
+                                     double* pk, int nbins, long long* kernels) {
+  if (!c || !kernels || (pk && nbins != c->edges_nbins)) return COLA_ERR_INVALID;
+  *kernels = 0;
+  cudaStream_t cap = nullptr;
+  COLA_TRY(cuda_status(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "stream"));
+  const cudaStream_t saved = c->stream;
+  const bool prof = c->prof;
+  long long launches[COLA_NUM_STAGES];
+  std::copy(c->stage_launches, c->stage_launches + COLA_NUM_STAGES, launches);
+  c->stream = cap;
+  c->prof = false;   // no timing events inside the capture
+  int st = cuda_status(cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed), "begin capture");
+  if (st == COLA_OK) {
+    const int run_st = cola_run(c, wn, s, v, psi1, psi2, pk, nbins);
+    cudaGraph_t g = nullptr;
+    const int end_st = cuda_status(cudaStreamEndCapture(cap, &g), "end capture");
+    st = run_st != COLA_OK ? run_st : end_st;
+    size_t nn = 0;
+    if (st == COLA_OK) st = cuda_status(cudaGraphGetNodes(g, nullptr, &nn), "graph nodes");
+    if (st == COLA_OK && nn) {
+      std::vector<cudaGraphNode_t> nodes(nn);
+      st = cuda_status(cudaGraphGetNodes(g, nodes.data(), &nn), "graph nodes");
+      for (size_t i = 0; st == COLA_OK && i < nn; ++i) {
+        cudaGraphNodeType ty;
+        st = cuda_status(cudaGraphNodeGetType(nodes[i], &ty), "node type");
+        if (st == COLA_OK && ty == cudaGraphNodeTypeKernel) ++*kernels;
+      }
+    }
+    if (g) cudaGraphDestroy(g);
+  }
+  c->stream = saved;
+  c->prof = prof;
+  std::copy(launches, launches + COLA_NUM_STAGES, c->stage_launches);
+  cudaStreamDestroy(cap);
+  return st;
 }
 
 extern "C" int cola_run_snapshots(cola_ctx* c, const float* wn, float* s, float* v, float* psi1, float* psi2,

@@ -191,6 +191,24 @@ def test_run_is_bit_reproducible():
         assert torch.equal(a[key], b[key]), key
 
 
+def test_run_kernel_count_counts_without_running():
+    """cola_run_kernel_count captures one cola_run, counts its kernels and leaves every buffer as it was."""
+    from paper_1507_05329_gb300 import ColaError
+    wn = dev(cola_inputs.white_noise(32, seed=1))
+    ctx = ctx_for(**SMALL)
+    out = ctx.run(wn, nbins=64)
+    ctx.sync()
+    before = {k: out[k].clone() for k in ("s", "v", "psi1", "psi2", "pk")}
+    k1 = ctx.run_kernel_count(wn, 64, out=out)
+    k2 = ctx.run_kernel_count(wn, 64, out=out)
+    ctx.sync()
+    assert k1 == k2 and k1 > 10 * 8, (k1, k2)   # at least eight kernels per COLA step
+    for key, val in before.items():
+        assert torch.equal(val, out[key]), key
+    with pytest.raises(ColaError):
+        ctx.run_kernel_count(wn, 32, out=dict(out, pk=torch.empty((3, 32), dtype=torch.float64, device="cuda")))
+
+
 @pytest.mark.parametrize("npd,nm,pipelined", [(32, 64, False), (32, 32, False), (24, 48, False), (32, 64, True),
                                                (24, 48, True)])
 def test_run_equals_a_loop_of_steps(npd, nm, pipelined):
