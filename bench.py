@@ -617,6 +617,8 @@ def run_ours(args):
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": peak_src,
                 "traffic": recorded_traffic(dom, args.workload),
+                "traffic_source": "ncu dram__bytes_read+write per launch from profiles/traffic.json"
+                                  + (", scaled 64x from the 256^3/384^3 capture" if args.workload == "large" else ""),
                 "algorithmic_bytes_per_launch": sb[dom], "avg_launch_ms": avg_ms}
     per_stage = {}
     for k in sb:
