@@ -312,6 +312,9 @@ int launch_c2r_rows(const FftPlan& p, const Grid3& g, float2* data, cudaStream_t
     const bool e8 = p.row_ept == 8 && g.n <= kTileElems / 2;
     const unsigned blocks = (unsigned)((nrows + (2LL << t.lw) - 1) / (2LL << t.lw));
     if (max_radix(fp) > 8) {
+      if (e8 ? plan3_c2r_launch<8>(fp, t.lw, blocks, t.threads, t.smem, data, g.pc, nrows, st)
+             : plan3_c2r_launch<16>(fp, t.lw, blocks, t.threads, t.smem, data, g.pc, nrows, st))
+        return check_launch("c2r_plan3");
       if (e8) fast_c2r_launch<16, 8>(fp, t.lw, blocks, t.threads, t.smem, data, g.pc, nrows, st);
       else fast_c2r_launch<16, 16>(fp, t.lw, blocks, t.threads, t.smem, data, g.pc, nrows, st);
     } else {
@@ -333,6 +336,10 @@ int launch_pencils(const FftPlan& p, const Grid3& g, int axis, int dir, float2* 
   FastPlan fp;
   if (fast_plan(p, &fp) && pipe_ok(p, g)) {
     const PipeShape ps = pipe_shape(g, p.pipe_kb, p.pipe_ept, p.pipe_inplace);
+    if (p.pipe_inplace && p.pipe_ept == 16 &&
+        plan3_pencils_launch(fp, ps.lw, ps.ctas, ps.threads, ps.smem, dir, data, jstride, ostride, g.nc, ps.nchunks,
+                             ps.ntiles, st))
+      return check_launch("pencils_plan3");
     if (max_radix(fp) > 8)
       pipe_pencils_launch<16>(fp, ps.lw, ps.ctas, ps.threads, ps.smem, dir, p.pipe_ept, p.pipe_inplace, data, jstride,
                               ostride, g.nc, ps.nchunks, ps.ntiles, st);
@@ -383,6 +390,10 @@ int launch_green_x(const FftPlan& p, const Grid3& g, const float2* in, float2* c
     const int nbuf = fp.nst >= 3 ? 2 : 1;
     const TileShape t = wide_shape(p, g, fast_shape(g.n, largest_pow2_le(g.nc), nbuf), nbuf);
     dim3 grid((g.nc + (1 << t.lw) - 1) >> t.lw, g.n);
+    if (plan3_green_launch(fp, t.lw, grid, t.threads, t.smem, in, out, g.pc, g.nc, dtab, g_scale, spec_out, st)) {
+      if (spec_saved) *spec_saved = spec_out != nullptr;
+      return check_launch("green_plan3");
+    }
     if (max_radix(fp) > 8)
       fast_green_launch<16, 16>(fp, t.lw, grid, t.threads, t.smem, in, out, g.pc, g.nc, dtab, g_scale, spec_out, st);
     else

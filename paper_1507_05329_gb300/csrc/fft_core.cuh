@@ -602,10 +602,19 @@ __device__ __forceinline__ void fwd_tile(const FastPlan& p, int lw, float2* a, f
   any_stage_e<false, DIR, MAXR, EPT>(p, m - 1, lw, SmemR{a, lw}, gdst, tid, nt);
 }
 
-// Inverse transform of a tile by the transposed stages m-1 .. 0.
-template <int DIR, int MAXR, class GSrc, class GDst, int EPT = kEpt>
+// Inverse transform of a tile by the transposed stages m-1 .. 0.  R0, R1, R2 > 0: the plan has exactly
+// three stages of those radices (compile-time stage code, the same butterflies in the same order).
+template <int DIR, int MAXR, class GSrc, class GDst, int EPT = kEpt, int R0 = 0, int R1 = 0, int R2 = 0>
 __device__ __forceinline__ void inv_tile(const FastPlan& p, int lw, float2* a, float2* b, const GSrc& gsrc,
                                          const GDst& gdst, int tid, int nt) {
+  if constexpr (R0 > 0) {
+    tr_stage<R2, DIR, GSrc, SmemW, EPT>(p, 2, lw, gsrc, SmemW{a, lw}, tid, nt);
+    __syncthreads();
+    tr_stage<R1, DIR, SmemR, SmemW, EPT>(p, 1, lw, SmemR{a, lw}, SmemW{b, lw}, tid, nt);
+    __syncthreads();
+    tr_stage<R0, DIR, SmemR, GDst, EPT>(p, 0, lw, SmemR{b, lw}, gdst, tid, nt);
+    return;
+  }
   const int m = p.nst;
   if (m == 1) {
     any_stage_e<true, DIR, MAXR, EPT>(p, 0, lw, gsrc, gdst, tid, nt);
@@ -741,7 +750,8 @@ struct PencilG2 {
 
 // Inverse x transform of the register-resident spectrum (times i D_x(k_x) when GRADX) into gout:
 // the transposed last stage straight from registers, then the remaining stages in shared memory.
-template <int RL, int MAXR, int EPT, bool GRADX, class GDst>
+// R0, R1 > 0: the plan has exactly three stages of radices R0, R1, RL (compile-time stage code).
+template <int RL, int MAXR, int EPT, bool GRADX, class GDst, int R0 = 0, int R1 = 0>
 __device__ __forceinline__ void green_inverse(const FastPlan& p, int lw, const float2 (&spec)[(EPT + RL - 1) / RL][RL],
                                               const float* __restrict__ dtab, const GDst& gout, float2* a, float2* b) {
   constexpr int kB = (EPT + RL - 1) / RL;
@@ -775,7 +785,13 @@ __device__ __forceinline__ void green_inverse(const FastPlan& p, int lw, const f
       else store_rows<RL>(gout, bb, nb, 0, lw, w, v);
     }
   }
-  if (m > 1) {
+  if constexpr (R0 > 0) {
+    __syncthreads();
+    tr_stage<R1, +1, SmemR, SmemW, EPT>(p, 1, lw, SmemR{cur, lw}, SmemW{nxt, lw}, tid, nt);
+    __syncthreads();
+    tr_stage<R0, +1, SmemR, GDst, EPT>(p, 0, lw, SmemR{nxt, lw}, gout, tid, nt);
+    __syncthreads();   // before the next inverse reuses the buffers
+  } else if (m > 1) {
     __syncthreads();
     for (int s = m - 2; s > 0; --s) {
       any_stage_e<true, +1, MAXR, EPT>(p, s, lw, SmemR{cur, lw}, SmemW{nxt, lw}, tid, nt);
@@ -792,7 +808,9 @@ __device__ __forceinline__ void green_inverse(const FastPlan& p, int lw, const f
 // x pass fused with Green function and gradient kernel, spectrum kept in registers between the
 // forward transform's last stage and the inverse transforms' first (transposed) stage.  EPT:
 // complex elements per thread per stage (16, or 8: twice the threads, half the registers held).
-template <int RL, int MAXR, int EPT>
+// R0, R1 > 0: the plan has exactly three stages of radices R0, R1, RL (compile-time stage code, the
+// same butterflies in the same order: bit-identical results).
+template <int RL, int MAXR, int EPT, int R0 = 0, int R1 = 0>
 __device__ __forceinline__ void green_body(const FastPlan& p, int lw, const float2* in, float2* out0, float2* out1,
                                            float2* out2, int pc, int nc, const float* __restrict__ dtab,
                                            float g_scale, float2* spec_out) {
@@ -810,7 +828,13 @@ __device__ __forceinline__ void green_body(const FastPlan& p, int lw, const floa
   float2 spec[kB][RL];
   // forward stages 0 .. m-2 (shared memory), last stage into registers
   const float2* last_in = nullptr;
-  if (m > 1) {
+  if constexpr (R0 > 0) {
+    fwd_stage<R0, -1, PencilG, SmemW, EPT>(p, 0, lw, gin, SmemW{a, lw}, tid, nt);
+    __syncthreads();
+    fwd_stage<R1, -1, SmemR, SmemW, EPT>(p, 1, lw, SmemR{a, lw}, SmemW{b, lw}, tid, nt);
+    __syncthreads();
+    last_in = b;
+  } else if (m > 1) {
     any_stage_e<false, -1, MAXR, EPT>(p, 0, lw, gin, SmemW{a, lw}, tid, nt);
     __syncthreads();
     for (int s = 1; s < m - 1; ++s) {
@@ -852,11 +876,11 @@ __device__ __forceinline__ void green_body(const FastPlan& p, int lw, const floa
   __syncthreads();   // the forward's shared buffers are free from here on
   // D_y(k_y) and D_z(k_z) are constant along an x pencil, so F_y and F_z are i D_y H and i D_z H of
   // one inverse H = IFFT_x(g delta): two inverse transforms instead of three
-  green_inverse<RL, MAXR, EPT, true>(p, lw, spec, dtab, PencilG{out0 + boff, jstride, nc - col0}, sm,
-                                     sm + fast_tile_elems(n, lw));
-  green_inverse<RL, MAXR, EPT, false>(p, lw, spec, dtab,
-                                      PencilG2{out1 + boff, out2 + boff, jstride, nc - col0, dtab[y], dtab + col0}, sm,
-                                      sm + fast_tile_elems(n, lw));
+  green_inverse<RL, MAXR, EPT, true, PencilG, R0, R1>(p, lw, spec, dtab, PencilG{out0 + boff, jstride, nc - col0}, sm,
+                                                      sm + fast_tile_elems(n, lw));
+  green_inverse<RL, MAXR, EPT, false, PencilG2, R0, R1>(
+      p, lw, spec, dtab, PencilG2{out1 + boff, out2 + boff, jstride, nc - col0, dtab[y], dtab + col0}, sm,
+      sm + fast_tile_elems(n, lw));
 }
 
 // =============================================================================================
@@ -950,6 +974,20 @@ void fast_green_launch(const fftk::FastPlan& fp, int lw, dim3 grid, int threads,
 template <int MAXR>
 void c2r_pipe_launch(const fftk::FastPlan& fp, int lw, int ctas, int threads, size_t smem, int ept, float2* data, int pc,
                      long long nrows, long long ntiles, cudaStream_t st);
+// The C2R rows of a 16 x 16 x {4, 5, 6} plan by a kernel specialised for the plan (EPT elements per
+// thread, as fast_c2r_launch<16, EPT>); false (nothing launched) for any other plan.
+template <int EPT>
+bool plan3_c2r_launch(const fftk::FastPlan& fp, int lw, unsigned blocks, int threads, size_t smem, float2* data, int pc,
+                      long long nrows, cudaStream_t st);
+// The fused Green pass of a 16 x 16 x {4, 5, 6} plan on tiles of 8 pencils (16 elements per thread,
+// kWideThreads threads) by a kernel specialised for the plan; false (nothing launched) otherwise.
+bool plan3_green_launch(const fftk::FastPlan& fp, int lw, dim3 grid, int threads, size_t smem, const float2* in,
+                        float2* const out[3], int pc, int nc, const float* dtab, float g_scale, float2* spec_out,
+                        cudaStream_t st);
+// The in-place pipelined pass of a 16 x 16 x {4, 5, 6} plan on tiles of 8 pencils (lw 3, kPipeThreads
+// threads) by a kernel specialised for the plan; false (nothing launched) for any other plan or shape.
+bool plan3_pencils_launch(const fftk::FastPlan& fp, int lw, int ctas, int threads, size_t smem, int dir, float2* data,
+                          long long jstride, long long ostride, int nc, int nchunks, int ntiles, cudaStream_t st);
 template <int MAXR>
 void pipe_pencils_launch(const fftk::FastPlan& fp, int lw, int ctas, int threads, size_t smem, int dir, int ept,
                          bool inplace, float2* data, long long jstride, long long ostride, int nc, int nchunks,
