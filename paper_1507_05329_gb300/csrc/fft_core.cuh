@@ -245,6 +245,45 @@ __device__ __forceinline__ float2 twid(const float2* __restrict__ tw, int t) {
   return v;
 }
 
+// Twiddle multiplies of butterfly k of stage s, v[r] *= w^(r k tstr_s) (conjugated for DIR > 0),
+// r = 1..R-1.  TWF: all R-1 twiddles are loaded before the first multiply (fewer registers held
+// across the loads in the strided y passes); else each load feeds its multiply.  Same products.
+template <int R, int DIR, bool TWF>
+__device__ __forceinline__ void apply_twiddles(const FastPlan& p, int s, int k, float2 (&v)[R]) {
+  const int tstr = p.tstr[s];
+  if constexpr (TWF) {
+    float2 t[R];
+#pragma unroll
+    for (int r = 1; r < R; ++r) t[r] = twid<DIR>(p.tw, r * k * tstr);
+#pragma unroll
+    for (int r = 1; r < R; ++r) v[r] = cmul(v[r], t[r]);
+  } else {
+#pragma unroll
+    for (int r = 1; r < R; ++r) v[r] = cmul(v[r], twid<DIR>(p.tw, r * k * tstr));
+  }
+}
+template <int R, int DIR, bool TWF>
+__device__ __forceinline__ void apply_twiddles2(const FastPlan& p, int s, int k, float2 (&va)[R], float2 (&vb)[R]) {
+  const int tstr = p.tstr[s];
+  if constexpr (TWF) {
+    float2 t[R];
+#pragma unroll
+    for (int r = 1; r < R; ++r) t[r] = twid<DIR>(p.tw, r * k * tstr);
+#pragma unroll
+    for (int r = 1; r < R; ++r) {
+      va[r] = cmul(va[r], t[r]);
+      vb[r] = cmul(vb[r], t[r]);
+    }
+  } else {
+#pragma unroll
+    for (int r = 1; r < R; ++r) {
+      const float2 t = twid<DIR>(p.tw, r * k * tstr);
+      va[r] = cmul(va[r], t);
+      vb[r] = cmul(vb[r], t);
+    }
+  }
+}
+
 struct SmemR {
   const float2* s;
   int lw;
@@ -351,11 +390,11 @@ __device__ __forceinline__ void store_rows2(const Dst& dst, int j0, int d, int d
   for (int r = 0; r < R; ++r) dst.st2(j0 + r * d, w, pack2(va[r], vb[r]));
 }
 
-template <int R, int DIR, class Src, class Dst, int EPT>
+template <int R, int DIR, class Src, class Dst, int EPT, bool TWF = false>
 __device__ __forceinline__ void fwd_stage_pairs(const FastPlan& p, int s, int lw, const Src& src, const Dst& dst,
                                                 int tid, int nthreads) {
   constexpr int kB = (EPT + 2 * R - 1) / (2 * R);
-  const int nb = p.n / R, lwp = lw - 1, total = nb << lwp, lns = p.lns[s], tstr = p.tstr[s];
+  const int nb = p.n / R, lwp = lw - 1, total = nb << lwp, lns = p.lns[s];
   const int wm = (1 << lwp) - 1, km = (1 << lns) - 1;
 #pragma unroll
   for (int i = 0; i < kB; ++i) {
@@ -364,14 +403,7 @@ __device__ __forceinline__ void fwd_stage_pairs(const FastPlan& p, int s, int lw
       const int w = (idx & wm) << 1, b = idx >> lwp, k = b & km;
       float2 va[R], vb[R];
       load_rows2<R>(src, b, nb, p.nbp[s], lw, w, va, vb);
-      if (lns) {
-#pragma unroll
-        for (int r = 1; r < R; ++r) {
-          const float2 t = twid<DIR>(p.tw, r * k * tstr);
-          va[r] = cmul(va[r], t);
-          vb[r] = cmul(vb[r], t);
-        }
-      }
+      if (lns) apply_twiddles2<R, DIR, TWF>(p, s, k, va, vb);
       Dft<R, DIR>::run(va);
       Dft<R, DIR>::run(vb);
       const int base = (((b >> lns) * R) << lns) + k;
@@ -380,11 +412,11 @@ __device__ __forceinline__ void fwd_stage_pairs(const FastPlan& p, int s, int lw
   }
 }
 
-template <int R, int DIR, class Src, class Dst, int EPT>
+template <int R, int DIR, class Src, class Dst, int EPT, bool TWF = false>
 __device__ __forceinline__ void tr_stage_pairs(const FastPlan& p, int s, int lw, const Src& src, const Dst& dst,
                                                int tid, int nthreads) {
   constexpr int kB = (EPT + 2 * R - 1) / (2 * R);
-  const int nb = p.n / R, lwp = lw - 1, total = nb << lwp, lns = p.lns[s], tstr = p.tstr[s];
+  const int nb = p.n / R, lwp = lw - 1, total = nb << lwp, lns = p.lns[s];
   const int wm = (1 << lwp) - 1, km = (1 << lns) - 1;
 #pragma unroll
   for (int i = 0; i < kB; ++i) {
@@ -396,29 +428,22 @@ __device__ __forceinline__ void tr_stage_pairs(const FastPlan& p, int s, int lw,
       load_rows2<R>(src, base, 1 << lns, p.nsp[s], lw, w, va, vb);
       Dft<R, DIR>::run(va);
       Dft<R, DIR>::run(vb);
-      if (lns) {
-#pragma unroll
-        for (int r = 1; r < R; ++r) {
-          const float2 t = twid<DIR>(p.tw, r * k * tstr);
-          va[r] = cmul(va[r], t);
-          vb[r] = cmul(vb[r], t);
-        }
-      }
+      if (lns) apply_twiddles2<R, DIR, TWF>(p, s, k, va, vb);
       store_rows2<R>(dst, b, nb, p.nbp[s], lw, w, va, vb);
     }
   }
 }
 
 // forward (decimation in time) stage s
-template <int R, int DIR, class Src, class Dst, int EPT = kEpt>
+template <int R, int DIR, class Src, class Dst, int EPT = kEpt, bool TWF = false>
 __device__ __forceinline__ void fwd_stage(const FastPlan& p, int s, int lw, const Src& src, const Dst& dst, int tid,
                                           int nthreads) {
   if (R <= 8 && lw >= 1 && 2 * R <= EPT) {   // pairs of columns: 2R elements per butterfly task
-    fwd_stage_pairs<R, DIR, Src, Dst, EPT>(p, s, lw, src, dst, tid, nthreads);
+    fwd_stage_pairs<R, DIR, Src, Dst, EPT, TWF>(p, s, lw, src, dst, tid, nthreads);
     return;
   }
   constexpr int kB = (EPT + R - 1) / R;
-  const int nb = p.n / R, total = nb << lw, lns = p.lns[s], tstr = p.tstr[s];
+  const int nb = p.n / R, total = nb << lw, lns = p.lns[s];
   const int wm = (1 << lw) - 1, km = (1 << lns) - 1;
 #pragma unroll
   for (int i = 0; i < kB; ++i) {
@@ -427,10 +452,7 @@ __device__ __forceinline__ void fwd_stage(const FastPlan& p, int s, int lw, cons
       const int w = idx & wm, b = idx >> lw, k = b & km;
       float2 v[R];
       load_rows<R>(src, b, nb, p.nbp[s], lw, w, v);
-      if (lns) {
-#pragma unroll
-        for (int r = 1; r < R; ++r) v[r] = cmul(v[r], twid<DIR>(p.tw, r * k * tstr));
-      }
+      if (lns) apply_twiddles<R, DIR, TWF>(p, s, k, v);
       Dft<R, DIR>::run(v);
       const int base = (((b >> lns) * R) << lns) + k;
       store_rows<R>(dst, base, 1 << lns, p.nsp[s], lw, w, v);
@@ -439,15 +461,15 @@ __device__ __forceinline__ void fwd_stage(const FastPlan& p, int s, int lw, cons
 }
 
 // transposed stage s (used in reverse order for the inverse transform)
-template <int R, int DIR, class Src, class Dst, int EPT = kEpt>
+template <int R, int DIR, class Src, class Dst, int EPT = kEpt, bool TWF = false>
 __device__ __forceinline__ void tr_stage(const FastPlan& p, int s, int lw, const Src& src, const Dst& dst, int tid,
                                          int nthreads) {
   if (R <= 8 && lw >= 1 && 2 * R <= EPT) {   // pairs of columns: 2R elements per butterfly task
-    tr_stage_pairs<R, DIR, Src, Dst, EPT>(p, s, lw, src, dst, tid, nthreads);
+    tr_stage_pairs<R, DIR, Src, Dst, EPT, TWF>(p, s, lw, src, dst, tid, nthreads);
     return;
   }
   constexpr int kB = (EPT + R - 1) / R;
-  const int nb = p.n / R, total = nb << lw, lns = p.lns[s], tstr = p.tstr[s];
+  const int nb = p.n / R, total = nb << lw, lns = p.lns[s];
   const int wm = (1 << lw) - 1, km = (1 << lns) - 1;
 #pragma unroll
   for (int i = 0; i < kB; ++i) {
@@ -458,10 +480,7 @@ __device__ __forceinline__ void tr_stage(const FastPlan& p, int s, int lw, const
       float2 v[R];
       load_rows<R>(src, base, 1 << lns, p.nsp[s], lw, w, v);
       Dft<R, DIR>::run(v);
-      if (lns) {
-#pragma unroll
-        for (int r = 1; r < R; ++r) v[r] = cmul(v[r], twid<DIR>(p.tw, r * k * tstr));
-      }
+      if (lns) apply_twiddles<R, DIR, TWF>(p, s, k, v);
       store_rows<R>(dst, b, nb, p.nbp[s], lw, w, v);
     }
   }
@@ -537,7 +556,7 @@ template <int R, int DIR, bool TR, int EPT>
 __device__ __forceinline__ void inplace_write(const FastPlan& p, int s, int lw, float2* buf, int tid, int nt,
                                               const float2 (&v)[EPT]) {
   constexpr int kB = EPT / R;
-  const int nb = p.n / R, total = nb << lw, lns = p.lns[s], tstr = p.tstr[s];
+  const int nb = p.n / R, total = nb << lw, lns = p.lns[s];
   const int wm = (1 << lw) - 1, km = (1 << lns) - 1;
   const SmemW dst{buf, lw};
 #pragma unroll
@@ -548,15 +567,9 @@ __device__ __forceinline__ void inplace_write(const FastPlan& p, int s, int lw, 
       float2 t[R];
 #pragma unroll
       for (int r = 0; r < R; ++r) t[r] = v[i * R + r];
-      if (!TR && lns) {
-#pragma unroll
-        for (int r = 1; r < R; ++r) t[r] = cmul(t[r], twid<DIR>(p.tw, r * k * tstr));
-      }
+      if (!TR && lns) apply_twiddles<R, DIR, true>(p, s, k, t);
       Dft<R, DIR>::run(t);
-      if (TR && lns) {
-#pragma unroll
-        for (int r = 1; r < R; ++r) t[r] = cmul(t[r], twid<DIR>(p.tw, r * k * tstr));
-      }
+      if (TR && lns) apply_twiddles<R, DIR, true>(p, s, k, t);
       if (TR) store_rows<R>(dst, b, nb, p.nbp[s], lw, w, t);
       else store_rows<R>(dst, (((b >> lns) * R) << lns) + k, 1 << lns, p.nsp[s], lw, w, t);
     }
