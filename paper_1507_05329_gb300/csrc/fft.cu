@@ -263,6 +263,11 @@ int launch_r2c_rows(const FftPlan& p, const Grid3& g, RowSource kind, const void
     const unsigned blocks = (unsigned)((nrows + (2LL << t.lw) - 1) / (2LL << t.lw));
     unsigned long long* acc = kind == kSrcFixedPoint ? mass_acc : nullptr;
     if (max_radix(fp) > 8) {
+      if (e8 ? plan3_r2c_launch<8>(fp, t.lw, blocks, t.threads, t.smem, kind, src, src_row_stride, scale, dst, g.pc,
+                                   nrows, acc, st)
+             : plan3_r2c_launch<16>(fp, t.lw, blocks, t.threads, t.smem, kind, src, src_row_stride, scale, dst, g.pc,
+                                    nrows, acc, st))
+        return check_launch("r2c_plan3");
       if (e8) fast_r2c_launch<16, 8>(fp, t.lw, blocks, t.threads, t.smem, kind, src, src_row_stride, scale, dst, g.pc, nrows, acc, st);
       else fast_r2c_launch<16, 16>(fp, t.lw, blocks, t.threads, t.smem, kind, src, src_row_stride, scale, dst, g.pc, nrows, acc, st);
     } else {

@@ -987,6 +987,12 @@ void fast_green_launch(const fftk::FastPlan& fp, int lw, dim3 grid, int threads,
 template <int MAXR>
 void c2r_pipe_launch(const fftk::FastPlan& fp, int lw, int ctas, int threads, size_t smem, int ept, float2* data, int pc,
                      long long nrows, long long ntiles, cudaStream_t st);
+// The R2C rows of a 16 x 16 x {4, 5, 6} plan by a kernel specialised for the plan (as
+// fast_r2c_launch<16, EPT>); false (nothing launched) for any other plan.
+template <int EPT>
+bool plan3_r2c_launch(const fftk::FastPlan& fp, int lw, unsigned blocks, int threads, size_t smem, int kind,
+                      const void* src, long long rs, float scale, float2* dst, int pc, long long nrows,
+                      unsigned long long* acc, cudaStream_t st);
 // The C2R rows of a 16 x 16 x {4, 5, 6} plan by a kernel specialised for the plan (EPT elements per
 // thread, as fast_c2r_launch<16, EPT>); false (nothing launched) for any other plan.
 template <int EPT>
