@@ -120,13 +120,19 @@ def test_adjoint_at_oracle_checkpoints(box, npd, nm, ng):
 
 
 # ---- end to end: GPU forward + GPU adjoint vs the oracle's gradient ------------------------------
+# relative L2 bar per (particles, mesh) side: about 3x the error measured on GB300
+GRADIENT_BAR = {(16, 32): 6e-4, (12, 24): 1.4e-2, (10, 30): 9e-4, (32, 64): 2.1e-3, (64, 128): 1.7e-3}
+
+
 @pytest.mark.parametrize("box,npd,nm,ng", CASES + [(256.0, 64, 128, 32)])
 def test_gradient_matches_oracle(box, npd, nm, ng):
     """dL/dw of L = sum (delta - delta_target)^2 through the autograd wrappers.  The GPU forward
     (fixed-point CIC, FP32) differs from the oracle's continuous-CIC FP64 forward by ~1e-4 cells,
     which moves the few particles that sit that close to a cell face to the other side of the
-    one-sided weight derivative.  Bar: loss within 1e-3 relative, gradient relative L2 error 2e-2
-    and correlation 0.999."""
+    one-sided weight derivative.  Bars: about 3x the errors measured on GB300 for each case (loss
+    relative error up to 1.1e-5; gradient relative L2 error 1.9e-4 to 4.5e-3, the largest on the
+    12^3 / 24^3 case, where a few particles sit within that distance of a cell face) and
+    correlation 0.999."""
     from paper_1507_05329_gb300.autograd import cola_run, grid_density
     p, w, target = _oracle_problem(box, npd, nm, ng)
     lref, gref = adjoint.gradient(w.astype(np.float64), p, ng, target)
@@ -136,11 +142,12 @@ def test_gradient_matches_oracle(box, npd, nm, ng):
     delta = grid_density(ctx, s, ng)
     loss = ((delta.double() - dev(target).double()) ** 2).sum()
     loss.backward()
-    assert float(loss.detach()) == pytest.approx(lref, rel=1e-3)
+    assert float(loss.detach()) == pytest.approx(lref, rel=5e-5)
     got = wt.grad.cpu().numpy()
     print(f"gradient vs oracle ({npd}^3, {nm}^3): rel L2 {rel_l2(got, gref):.3e}, loss rel "
           f"{abs(float(loss.detach()) / lref - 1):.2e}")
-    assert rel_l2(got, gref) < 2e-2
+    bar = GRADIENT_BAR[(npd, nm)]
+    assert rel_l2(got, gref) < bar
     assert np.corrcoef(got, gref)[0, 1] > 0.999
 
 
