@@ -197,19 +197,36 @@ __global__ void __launch_bounds__(kThreads) k_bin_scatter(ParticleGeom pg, BinGe
                                                           unsigned* ent_p, unsigned* ent_s) {
   const int np = pg.np;
   const long long nrows = (long long)np * np;
+  constexpr int U = 2;   // records in flight per thread: their loads, then their offset lookups
   for (long long row = blockIdx.x; row < nrows; row += gridDim.x) {
     const int qx = (int)(row / np), qy = (int)(row - (long long)qx * np);
-    for (int qz = threadIdx.x; qz < np; qz += blockDim.x) {
-      const unsigned long long r = __ldcs(rec + row * np + qz);
-      const unsigned key = (unsigned)r & ((1u << 26) - 1u), flags = ((unsigned)r >> 26) & 7u;
-      const unsigned packed = pack_q(qx, qy, qz);
-      ent_p[off_p[key] + (unsigned)(r >> 32)] = packed;
-      if (flags) {
-        int k[8];
-        keys_from_record(b, key, flags, k);
+    for (int q0 = threadIdx.x; q0 < np; q0 += U * blockDim.x) {
+      unsigned long long r[U];
+      unsigned base[U];
 #pragma unroll
-        for (int e = 1; e < 8; ++e)
-          if (k[e] >= 0) ent_s[atomicAdd(cur_s + k[e], 1u)] = packed;
+      for (int u = 0; u < U; ++u) {
+        const int qz = q0 + u * (int)blockDim.x;
+        r[u] = qz < np ? __ldcs(rec + row * np + qz) : 0ULL;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int qz = q0 + u * (int)blockDim.x;
+        base[u] = qz < np ? __ldg(off_p + ((unsigned)r[u] & ((1u << 26) - 1u))) : 0u;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int qz = q0 + u * (int)blockDim.x;
+        if (qz >= np) continue;
+        const unsigned key = (unsigned)r[u] & ((1u << 26) - 1u), flags = ((unsigned)r[u] >> 26) & 7u;
+        const unsigned packed = pack_q(qx, qy, qz);
+        ent_p[base[u] + (unsigned)(r[u] >> 32)] = packed;
+        if (flags) {
+          int k[8];
+          keys_from_record(b, key, flags, k);
+#pragma unroll
+          for (int e = 1; e < 8; ++e)
+            if (k[e] >= 0) ent_s[atomicAdd(cur_s + k[e], 1u)] = packed;
+        }
       }
     }
   }
