@@ -238,6 +238,16 @@ struct FastPlan {
   const float2* tw;
 };
 
+// The three-stage plans that have kernels specialised for them: 1 = 16 x 8 x 8 (1024 points),
+// 2 = 16 x 16 x 5 (1280), 3 = 16 x 16 x 6 (1536); 0 for any other plan.
+inline int plan3_id(const FastPlan& fp) {
+  if (fp.nst != 3 || fp.radix[0] != 16) return 0;
+  if (fp.radix[1] == 8 && fp.radix[2] == 8) return 1;
+  if (fp.radix[1] == 16 && fp.radix[2] == 5) return 2;
+  if (fp.radix[1] == 16 && fp.radix[2] == 6) return 3;
+  return 0;
+}
+
 template <int DIR>
 __device__ __forceinline__ float2 twid(const float2* __restrict__ tw, int t) {
   float2 v = __ldg(&tw[t]);
@@ -987,24 +997,24 @@ void fast_green_launch(const fftk::FastPlan& fp, int lw, dim3 grid, int threads,
 template <int MAXR>
 void c2r_pipe_launch(const fftk::FastPlan& fp, int lw, int ctas, int threads, size_t smem, int ept, float2* data, int pc,
                      long long nrows, long long ntiles, cudaStream_t st);
-// The R2C rows of a 16 x 16 x {4, 5, 6} plan by a kernel specialised for the plan (as
+// The R2C rows of a plan with specialised kernels (plan3_id) by its kernel (as
 // fast_r2c_launch<16, EPT>); false (nothing launched) for any other plan.
 template <int EPT>
 bool plan3_r2c_launch(const fftk::FastPlan& fp, int lw, unsigned blocks, int threads, size_t smem, int kind,
                       const void* src, long long rs, float scale, float2* dst, int pc, long long nrows,
                       unsigned long long* acc, cudaStream_t st);
-// The C2R rows of a 16 x 16 x {4, 5, 6} plan by a kernel specialised for the plan (EPT elements per
+// The C2R rows of a plan with specialised kernels (plan3_id) by its kernel (EPT elements per
 // thread, as fast_c2r_launch<16, EPT>); false (nothing launched) for any other plan.
 template <int EPT>
 bool plan3_c2r_launch(const fftk::FastPlan& fp, int lw, unsigned blocks, int threads, size_t smem, float2* data, int pc,
                       long long nrows, cudaStream_t st);
-// The fused Green pass of a 16 x 16 x {4, 5, 6} plan on tiles of 8 pencils (16 elements per thread,
-// kWideThreads threads) by a kernel specialised for the plan; false (nothing launched) otherwise.
+// The fused Green pass of a plan with specialised kernels (plan3_id) on tiles of 8 pencils (16 elements
+// per thread) by its kernel; false (nothing launched) otherwise.
 bool plan3_green_launch(const fftk::FastPlan& fp, int lw, dim3 grid, int threads, size_t smem, const float2* in,
                         float2* const out[3], int pc, int nc, const float* dtab, float g_scale, float2* spec_out,
                         cudaStream_t st);
-// The in-place pipelined pass of a 16 x 16 x {4, 5, 6} plan on tiles of 8 pencils (lw 3, kPipeThreads
-// threads) by a kernel specialised for the plan; false (nothing launched) for any other plan or shape.
+// The in-place pipelined pass of a plan with specialised kernels (plan3_id) on tiles of 8 pencils (lw 3,
+// 16 elements per thread) by its kernel; false (nothing launched) for any other plan or shape.
 bool plan3_pencils_launch(const fftk::FastPlan& fp, int lw, int ctas, int threads, size_t smem, int dir, float2* data,
                           long long jstride, long long ostride, int nc, int nchunks, int ntiles, cudaStream_t st);
 template <int MAXR>
