@@ -206,6 +206,24 @@ int inverse3d(cola_ctx* c, const Grid3& g, const FftPlan& p, float2* b) {
   return STAGED(kStInvZ, launch_c2r_rows(p, g, b, c->stream));
 }
 
+// A 2LPT field: inverse3d of mul times the lattice spectrum src, into dst, and, with particles, into
+// that particle array (dense, times scale).  Where the plan allows, the multiply rides in the first
+// inverse pass and the last pass writes the particle layout itself; else separate kernels do.
+int inverse3d_mul(cola_ctx* c, const Grid3& g, const FftPlan& p, const float2* src, const IcMul& mul, float2* dst,
+                  float scale = 1.0f, float* particles = nullptr) {
+  if (pencils_x_mul_ok(p, g)) {
+    COLA_TRY(STAGED(kStFwdX, launch_pencils_x_mul(p, g, src, mul, dst, c->stream)));
+  } else {
+    COLA_TRY(STAGED(kStIc, launch_ic_multiply(g, src, dst, (IcField)mul.kind, mul.ci, mul.cj, mul.scale, c->stream)));
+    COLA_TRY(STAGED(kStFwdX, launch_pencils(p, g, 0, +1, dst, c->stream)));
+  }
+  COLA_TRY(STAGED(kStInvY, launch_pencils(p, g, 1, +1, dst, c->stream)));
+  if (!particles) return STAGED(kStInvZ, launch_c2r_rows(p, g, dst, c->stream));
+  if (c2r_rows_dense_ok(p, g)) return STAGED(kStInvZ, launch_c2r_rows_dense(p, g, dst, scale, particles, c->stream));
+  COLA_TRY(STAGED(kStInvZ, launch_c2r_rows(p, g, dst, c->stream)));
+  return STAGED(kStIc, launch_ic_to_particles(g, dst, scale, particles, c->stream));
+}
+
 int forward3d_yx(cola_ctx* c, const Grid3& g, const FftPlan& p, float2* b) {
   COLA_TRY(STAGED(kStFwdY, launch_pencils(p, g, 1, -1, b, c->stream)));
   return STAGED(kStFwdX, launch_pencils(p, g, 0, -1, b, c->stream));
@@ -459,15 +477,12 @@ extern "C" int cola_ic_2lpt(cola_ctx* c, const float* wn, float* s, float* v, fl
   COLA_TRY(STAGED(kStIc, launch_ic_amplitude(g, B[0], c->amp_m2, c->stream)));
   // Psi1 = i k delta_L / k^2
   for (int j = 0; j < 3; ++j) {
-    COLA_TRY(STAGED(kStIc, launch_ic_multiply(g, B[0], B[7], kIcPsi1, j, 0, 1.0f, c->stream)));
-    COLA_TRY(inverse3d(c, g, P, B[7]));
-    COLA_TRY(STAGED(kStIc, launch_ic_to_particles(g, B[7], r, psi1 + j * n, c->stream)));
+    COLA_TRY(inverse3d_mul(c, g, P, B[0], IcMul{kIcPsi1, j, 0, 1.0f}, B[7], r, psi1 + j * n));
   }
   // phi1_ij = k_i k_j delta_L / k^2 in real space, then the second-order source
   const int pairs[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
   for (int h = 0; h < 6; ++h) {
-    COLA_TRY(STAGED(kStIc, launch_ic_multiply(g, B[0], B[1 + h], kIcHess, pairs[h][0], pairs[h][1], 1.0f, c->stream)));
-    COLA_TRY(inverse3d(c, g, P, B[1 + h]));
+    COLA_TRY(inverse3d_mul(c, g, P, B[0], IcMul{kIcHess, pairs[h][0], pairs[h][1], 1.0f}, B[1 + h]));
   }
   float2* const hs[6] = {B[1], B[2], B[3], B[4], B[5], B[6]};
   COLA_TRY(STAGED(kStIc, launch_ic_source(g, hs, B[7], c->stream)));
@@ -476,9 +491,7 @@ extern "C" int cola_ic_2lpt(cola_ctx* c, const float* wn, float* s, float* v, fl
   // Psi2 = -i k S(k) / k^2
   const float inv_n3 = (float)(1.0 / ((double)g.n * g.n * g.n));
   for (int j = 0; j < 3; ++j) {
-    COLA_TRY(STAGED(kStIc, launch_ic_multiply(g, B[7], B[1], kIcPsi2, j, 0, inv_n3, c->stream)));
-    COLA_TRY(inverse3d(c, g, P, B[1]));
-    COLA_TRY(STAGED(kStIc, launch_ic_to_particles(g, B[1], r, psi2 + j * n, c->stream)));
+    COLA_TRY(inverse3d_mul(c, g, P, B[7], IcMul{kIcPsi2, j, 0, inv_n3}, B[1], r, psi2 + j * n));
   }
   const StepScalars& s0 = c->steps[0];
   return STAGED(kStIc, launch_ic_positions(n, psi1, psi2, (float)s0.d1, (float)s0.d2, s, v, c->stream));

@@ -101,6 +101,19 @@ int launch_r2c_rows(const FftPlan& p, const Grid3& g, RowSource kind, const void
                     unsigned long long* mass_acc = nullptr);
 // Inverse C2R along z, in place on a complex grid (real rows of stride 2*pc floats).
 int launch_c2r_rows(const FftPlan& p, const Grid3& g, float2* data, cudaStream_t st);
+// The C2R rows of data (not modified) written to out as dense rows of n floats times scale, where the
+// plan has a specialised kernel for it (c2r_rows_dense_ok); the same floats as launch_c2r_rows then
+// launch_ic_to_particles.
+bool c2r_rows_dense_ok(const FftPlan& p, const Grid3& g);
+// The inverse x pass of mul times the lattice spectrum src into dst (src unchanged) where the plan has
+// a specialised in-place pipelined kernel for it (pencils_x_mul_ok); the same floats as
+// launch_ic_multiply followed by launch_pencils(axis 0, +1).
+struct IcMul;
+bool pencils_x_mul_ok(const FftPlan& p, const Grid3& g);
+int launch_pencils_x_mul(const FftPlan& p, const Grid3& g, const float2* src, const IcMul& mul, float2* dst,
+                         cudaStream_t st);
+int launch_c2r_rows_dense(const FftPlan& p, const Grid3& g, const float2* data, float scale, float* out,
+                          cudaStream_t st);
 // C2C along y (axis 1) or x (axis 0) of the complex grid; dir = -1 forward, +1 inverse.
 int launch_pencils(const FftPlan& p, const Grid3& g, int axis, int dir, float2* data,
                    cudaStream_t st);
@@ -264,6 +277,45 @@ int launch_gather_tiles(const ParticleGeom& pg, const BinGeom& b, const BinBuffe
 
 // 2LPT helpers on the lattice grid (side np).
 enum IcField { kIcPsi1 = 0, kIcHess = 1, kIcPsi2 = 2 };
+// One 2LPT spectral multiply: field kind, components ci, cj and a scale (see ic_multiply_mode).
+struct IcMul {
+  int kind, ci, cj;
+  float scale;
+};
+#ifdef __CUDACC__
+__device__ __forceinline__ int signed_mode(int i, int n) { return i < n / 2 ? i : i - n; }
+// The 2LPT multiplier of mode m (integer wave numbers, m[2] >= 0) applied to z: Psi1_j = i k_j / k^2,
+// Psi2_j = -i k_j / k^2 (times scale), Hessian_ij = k_i k_j / k^2; the Nyquist plane of an odd
+// derivative is zeroed and k = 0 gives 0.  One definition for the multiply kernel and the inverse
+// pass that fuses it, so both compute the same floats.
+__device__ __forceinline__ float2 ic_multiply_mode(float2 z, const int (&m)[3], int n, const IcMul& mp) {
+  const float kf = 6.283185307179586f / n;
+  const float m2 = (float)m[0] * m[0] + (float)m[1] * m[1] + (float)m[2] * m[2];
+  float2 out = make_float2(0.f, 0.f);
+  if (m2 > 0.f) {
+    const float inv_k2 = 1.0f / (m2 * kf * kf);
+    const int nyq = n / 2;
+    const float koi = (m[mp.ci] == nyq || m[mp.ci] == -nyq) ? 0.f : m[mp.ci] * kf;
+    if (mp.kind == kIcPsi1) {
+      const float c = koi * inv_k2 * mp.scale;   // i c z
+      out = make_float2(-c * z.y, c * z.x);
+    } else if (mp.kind == kIcPsi2) {
+      const float c = -koi * inv_k2 * mp.scale;
+      out = make_float2(-c * z.y, c * z.x);
+    } else {
+      float kk;
+      if (mp.ci == mp.cj) kk = (m[mp.ci] * kf) * (m[mp.ci] * kf);
+      else {
+        const float koj = (m[mp.cj] == nyq || m[mp.cj] == -nyq) ? 0.f : m[mp.cj] * kf;
+        kk = koi * koj;
+      }
+      const float c = kk * inv_k2 * mp.scale;
+      out = make_float2(c * z.x, c * z.y);
+    }
+  }
+  return out;
+}
+#endif
 int launch_ic_amplitude(const Grid3& g, float2* wk, const float* amp_m2, cudaStream_t st);
 int launch_ic_multiply(const Grid3& g, const float2* src, float2* dst, IcField kind, int i, int j,
                        float scale, cudaStream_t st, bool accumulate = false);

@@ -334,6 +334,44 @@ int launch_c2r_rows(const FftPlan& p, const Grid3& g, float2* data, cudaStream_t
   return check_launch("c2r_rows");
 }
 
+bool pencils_x_mul_ok(const FftPlan& p, const Grid3& g) {
+  FastPlan fp;
+  if (!(fast_plan(p, &fp) && pipe_ok(p, g) && p.pipe_inplace && p.pipe_ept == 16 && plan3_id(fp) != 0)) return false;
+  const PipeShape ps = pipe_shape(g, p.pipe_kb, p.pipe_ept, p.pipe_inplace);
+  return ps.lw == 3 && ps.threads * 16 == (g.n << ps.lw);
+}
+
+int launch_pencils_x_mul(const FftPlan& p, const Grid3& g, const float2* src, const IcMul& mul, float2* dst,
+                         cudaStream_t st) {
+  FastPlan fp;
+  if (!pencils_x_mul_ok(p, g) || !fast_plan(p, &fp)) return COLA_ERR_INVALID;
+  const PipeShape ps = pipe_shape(g, p.pipe_kb, p.pipe_ept, p.pipe_inplace);
+  const long long plane = (long long)g.n * g.pc;
+  if (!plan3_pencils_launch(fp, ps.lw, ps.ctas, ps.threads, ps.smem, +1, dst, plane, g.pc, g.nc, ps.nchunks, ps.ntiles,
+                            st, src, &mul))
+    return COLA_ERR_INVALID;
+  return check_launch("pencils_x_mul");
+}
+
+bool c2r_rows_dense_ok(const FftPlan& p, const Grid3& g) {
+  FastPlan fp;
+  return !p.row_pipe && fast_plan(p, &fp) && plan3_id(fp) != 0 && g.nc >= 2;
+}
+
+int launch_c2r_rows_dense(const FftPlan& p, const Grid3& g, const float2* data, float scale, float* out,
+                          cudaStream_t st) {
+  FastPlan fp;
+  if (!c2r_rows_dense_ok(p, g) || !fast_plan(p, &fp)) return COLA_ERR_INVALID;
+  const long long nrows = (long long)g.rows();
+  const TileShape t = row_shape(p.row_ept, g, 2);
+  const bool e8 = p.row_ept == 8 && g.n <= kTileElems / 2;
+  const unsigned blocks = (unsigned)((nrows + (2LL << t.lw) - 1) / (2LL << t.lw));
+  float2* d = const_cast<float2*>(data);   // only read when out is given
+  const bool ok = e8 ? plan3_c2r_launch<8>(fp, t.lw, blocks, t.threads, t.smem, d, g.pc, nrows, st, out, scale)
+                     : plan3_c2r_launch<16>(fp, t.lw, blocks, t.threads, t.smem, d, g.pc, nrows, st, out, scale);
+  return ok ? check_launch("c2r_dense") : COLA_ERR_INVALID;
+}
+
 int launch_pencils(const FftPlan& p, const Grid3& g, int axis, int dir, float2* data, cudaStream_t st) {
   const long long plane = (long long)g.n * g.pc;
   const long long jstride = axis == 1 ? g.pc : plane;

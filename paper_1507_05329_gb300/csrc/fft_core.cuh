@@ -743,6 +743,21 @@ struct RealPairDst {   // (re, im) -> real rows (2w, 2w+1)
   }
 };
 
+struct DenseScaledDst {   // (re, im) -> scale x (re, im) in dense rows (2w, 2w+1) of n floats
+  float* out;
+  long long n, row0, nrows;
+  float scale;
+  __device__ __forceinline__ void operator()(int j, int w, float2 v) const {
+    const long long ra = row0 + 2 * w;
+    if (ra < nrows) out[ra * n + j] = v.x * scale;
+    if (ra + 1 < nrows) out[(ra + 1) * n + j] = v.y * scale;
+  }
+  __device__ __forceinline__ void st2(int j, int w, float4 v) const {
+    (*this)(j, w, make_float2(v.x, v.y));
+    (*this)(j, w + 1, make_float2(v.z, v.w));
+  }
+};
+
 __device__ __forceinline__ int fast_tile_elems(int n, int lw) { return (n + n / 16 + 1) << lw; }
 
 // Writes i dy v to base1 and i dz[w] v to base2 (W adjacent columns of two strided pencils).
@@ -1005,9 +1020,11 @@ bool plan3_r2c_launch(const fftk::FastPlan& fp, int lw, unsigned blocks, int thr
                       unsigned long long* acc, cudaStream_t st);
 // The C2R rows of a plan with specialised kernels (plan3_id) by its kernel (EPT elements per
 // thread, as fast_c2r_launch<16, EPT>); false (nothing launched) for any other plan.
+// out != nullptr: the real rows go to out as dense rows of n floats times scale (the particle
+// arrays' layout) and data is only read.
 template <int EPT>
 bool plan3_c2r_launch(const fftk::FastPlan& fp, int lw, unsigned blocks, int threads, size_t smem, float2* data, int pc,
-                      long long nrows, cudaStream_t st);
+                      long long nrows, cudaStream_t st, float* out = nullptr, float scale = 1.0f);
 // The fused Green pass of a plan with specialised kernels (plan3_id) on tiles of 8 pencils (16 elements
 // per thread) by its kernel; false (nothing launched) otherwise.
 bool plan3_green_launch(const fftk::FastPlan& fp, int lw, dim3 grid, int threads, size_t smem, const float2* in,
@@ -1015,8 +1032,11 @@ bool plan3_green_launch(const fftk::FastPlan& fp, int lw, dim3 grid, int threads
                         cudaStream_t st);
 // The in-place pipelined pass of a plan with specialised kernels (plan3_id) on tiles of 8 pencils (lw 3,
 // 16 elements per thread) by its kernel; false (nothing launched) for any other plan or shape.
+// mul (inverse passes only): the tile is read from src and multiplied by the 2LPT factor *mul of its
+// mode before the transform, which is written to data.
 bool plan3_pencils_launch(const fftk::FastPlan& fp, int lw, int ctas, int threads, size_t smem, int dir, float2* data,
-                          long long jstride, long long ostride, int nc, int nchunks, int ntiles, cudaStream_t st);
+                          long long jstride, long long ostride, int nc, int nchunks, int ntiles, cudaStream_t st,
+                          const float2* src = nullptr, const IcMul* mul = nullptr);
 template <int MAXR>
 void pipe_pencils_launch(const fftk::FastPlan& fp, int lw, int ctas, int threads, size_t smem, int dir, int ept,
                          bool inplace, float2* data, long long jstride, long long ostride, int nc, int nchunks,

@@ -170,7 +170,6 @@ __global__ void k_mesh_sum(const unsigned long long* __restrict__ rho, long long
 }
 
 // ---- 2LPT helpers on the lattice grid (side n = np, half spectrum rows of pc) --------------
-__device__ __forceinline__ int signed_mode(int i, int n) { return i < n / 2 ? i : i - n; }
 
 __global__ void k_ic_amplitude(int n, int pc, int nc, float2* wk, const float* __restrict__ amp_m2) {
   const long long total = (long long)n * n * nc;
@@ -189,39 +188,15 @@ __global__ void k_ic_amplitude(int n, int pc, int nc, float2* wk, const float* _
 // dst(k) = M(k) src(k): Psi1 component i: i kodd_i / k^2; Hessian (i, j): k_i k_j / k^2 (diagonal
 // uses the full k_i, off-diagonal the Nyquist-zeroed kodd); Psi2 component i: -i kodd_i / k^2.
 // k in radians per lattice spacing, times 'scale'.
-__global__ void k_ic_multiply(int n, int pc, int nc, const float2* __restrict__ src, float2* dst, int kind,
-                              int ci, int cj, float scale, int accumulate) {
+__global__ void k_ic_multiply(int n, int pc, int nc, const float2* __restrict__ src, float2* dst, IcMul mp,
+                              int accumulate) {
   const long long total = (long long)n * n * nc;
-  const float kf = 6.283185307179586f / n;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
     const int kz = (int)(t % nc);
     const long long row = t / nc;
-    int m[3] = {signed_mode((int)(row / n), n), signed_mode((int)(row % n), n), kz};
-    const float m2 = (float)m[0] * m[0] + (float)m[1] * m[1] + (float)m[2] * m[2];
-    const float2 z = src[row * pc + kz];
-    float2 out = make_float2(0.f, 0.f);
-    if (m2 > 0.f) {
-      const float inv_k2 = 1.0f / (m2 * kf * kf);
-      const int nyq = n / 2;
-      const float koi = (m[ci] == nyq || m[ci] == -nyq) ? 0.f : m[ci] * kf;
-      if (kind == kIcPsi1) {
-        const float c = koi * inv_k2 * scale;              // i c z
-        out = make_float2(-c * z.y, c * z.x);
-      } else if (kind == kIcPsi2) {
-        const float c = -koi * inv_k2 * scale;
-        out = make_float2(-c * z.y, c * z.x);
-      } else {
-        float kk;
-        if (ci == cj) kk = (m[ci] * kf) * (m[ci] * kf);
-        else {
-          const float koj = (m[cj] == nyq || m[cj] == -nyq) ? 0.f : m[cj] * kf;
-          kk = koi * koj;
-        }
-        const float c = kk * inv_k2 * scale;
-        out = make_float2(c * z.x, c * z.y);
-      }
-    }
+    const int m[3] = {signed_mode((int)(row / n), n), signed_mode((int)(row % n), n), kz};
+    float2 out = ic_multiply_mode(src[row * pc + kz], m, n, mp);
     if (accumulate) {
       const float2 o = dst[row * pc + kz];
       out = make_float2(out.x + o.x, out.y + o.y);
@@ -552,8 +527,9 @@ int launch_ic_amplitude(const Grid3& g, float2* wk, const float* amp_m2, cudaStr
 
 int launch_ic_multiply(const Grid3& g, const float2* src, float2* dst, IcField kind, int i, int j, float scale,
                        cudaStream_t st, bool accumulate) {
-  k_ic_multiply<<<grid_for((long long)g.rows() * g.nc, 256), 256, 0, st>>>(g.n, g.pc, g.nc, src, dst, (int)kind,
-                                                                           i, j, scale, accumulate ? 1 : 0);
+  k_ic_multiply<<<grid_for((long long)g.rows() * g.nc, 256), 256, 0, st>>>(g.n, g.pc, g.nc, src, dst,
+                                                                           IcMul{(int)kind, i, j, scale},
+                                                                           accumulate ? 1 : 0);
   return check_launch("ic_multiply");
 }
 
