@@ -824,11 +824,18 @@ __device__ __forceinline__ void green_inverse(const FastPlan& p, int lw, const f
     }
   }
   if constexpr (R0 > 0) {
+    // the middle stage in place in cur (its values read into registers, then written back): the other
+    // buffer stays free for the parked spectrum
     __syncthreads();
-    tr_stage<R1, +1, SmemR, SmemW, EPT>(p, 1, lw, SmemR{cur, lw}, SmemW{nxt, lw}, tid, nt);
+    {
+      float2 w16[EPT];
+      inplace_read<R1, true, EPT>(p, 1, lw, cur, tid, nt, w16);
+      __syncthreads();
+      inplace_write<R1, +1, true, EPT>(p, 1, lw, cur, tid, nt, w16);
+    }
     __syncthreads();
-    tr_stage<R0, +1, SmemR, GDst, EPT>(p, 0, lw, SmemR{nxt, lw}, gout, tid, nt);
-    __syncthreads();   // before the next inverse reuses the buffers
+    tr_stage<R0, +1, SmemR, GDst, EPT>(p, 0, lw, SmemR{cur, lw}, gout, tid, nt);
+    __syncthreads();   // before the next inverse reuses the buffer
   } else if (m > 1) {
     __syncthreads();
     for (int s = m - 2; s > 0; --s) {
@@ -914,11 +921,38 @@ __device__ __forceinline__ void green_body(const FastPlan& p, int lw, const floa
   __syncthreads();   // the forward's shared buffers are free from here on
   // D_y(k_y) and D_z(k_z) are constant along an x pencil, so F_y and F_z are i D_y H and i D_z H of
   // one inverse H = IFFT_x(g delta): two inverse transforms instead of three
-  green_inverse<RL, MAXR, EPT, true, PencilG, R0, R1>(p, lw, spec, dtab, PencilG{out0 + boff, jstride, nc - col0}, sm,
-                                                      sm + fast_tile_elems(n, lw));
-  green_inverse<RL, MAXR, EPT, false, PencilG2, R0, R1>(
-      p, lw, spec, dtab, PencilG2{out1 + boff, out2 + boff, jstride, nc - col0, dtab[y], dtab + col0}, sm,
-      sm + fast_tile_elems(n, lw));
+  if constexpr (R0 > 0) {
+    // three-stage plans: the spectrum is parked in the second buffer (element (r, idx) at r total + idx)
+    // while the first inverse runs in place in the first, so it is not held in registers across it
+    float2* park = sm + fast_tile_elems(n, lw);
+#pragma unroll
+    for (int i = 0; i < kB; ++i) {
+      const int idx = tid + i * nt;
+      if (idx < total) {
+#pragma unroll
+        for (int r = 0; r < RL; ++r) park[r * total + idx] = spec[i][r];
+      }
+    }
+    green_inverse<RL, MAXR, EPT, true, PencilG, R0, R1>(p, lw, spec, dtab, PencilG{out0 + boff, jstride, nc - col0}, sm,
+                                                        nullptr);
+    float2 spec2[kB][RL];
+#pragma unroll
+    for (int i = 0; i < kB; ++i) {
+      const int idx = tid + i * nt;
+      if (idx < total) {
+#pragma unroll
+        for (int r = 0; r < RL; ++r) spec2[i][r] = park[r * total + idx];
+      }
+    }
+    green_inverse<RL, MAXR, EPT, false, PencilG2, R0, R1>(
+        p, lw, spec2, dtab, PencilG2{out1 + boff, out2 + boff, jstride, nc - col0, dtab[y], dtab + col0}, sm, nullptr);
+  } else {
+    green_inverse<RL, MAXR, EPT, true, PencilG, R0, R1>(p, lw, spec, dtab, PencilG{out0 + boff, jstride, nc - col0},
+                                                        sm, sm + fast_tile_elems(n, lw));
+    green_inverse<RL, MAXR, EPT, false, PencilG2, R0, R1>(
+        p, lw, spec, dtab, PencilG2{out1 + boff, out2 + boff, jstride, nc - col0, dtab[y], dtab + col0}, sm,
+        sm + fast_tile_elems(n, lw));
+  }
 }
 
 // =============================================================================================
