@@ -488,6 +488,60 @@ __device__ __forceinline__ void gather_stage(float* fsm, const BinGeom& b, int n
   asm volatile("cp.async.commit_group;\n" ::: "memory");
 }
 
+constexpr int kBulkWaitLimit = 1 << 22;   // polls of a staging barrier before the CTA gives up
+
+// Stage a tile's forces as gather_stage does, by bulk copies: one cp.async.bulk of TZ cells per force
+// row (3 (T+1)^2 rows, a row per thread), all completing on the mbarrier at bar_sa, plus each row's
+// periodic halo cell by a 4-byte cp.async (committed as one group).  Rows start 16-byte aligned (z0 a
+// multiple of TZ >= 4, rows of 2 pc floats with pc even) and TZ cells are a multiple of 16 bytes.
+// Called by every thread of the block; contains a barrier.
+template <int LT, int LZ>
+__device__ __forceinline__ void gather_stage_bulk(float* fsm, unsigned bar_sa, const BinGeom& b, int nm,
+                                                  const GatherTile& t, const float* __restrict__ f0,
+                                                  const float* __restrict__ f1, const float* __restrict__ f2,
+                                                  long long rs) {
+  const int hx = (1 << (LT ? LT : b.lt)) + 1, zl = 1 << (LZ ? LZ : b.lz), hp = (zl + 1 + 3) & ~3;
+  const int rows = 3 * hx * hx;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar_sa) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(bar_sa),
+                 "r"(rows * zl * 4)
+                 : "memory");
+  }
+  __syncthreads();   // the barrier expects every row's bytes before any copy is issued
+  const int gzz = t.z0 + zl == nm ? 0 : t.z0 + zl;
+  for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+    const int comp = r / (hx * hx), col = r - comp * hx * hx;
+    const int lx = col / hx, ly = col - lx * hx;
+    int gx = t.x0 + lx, gy = t.y0 + ly;
+    if (gx >= nm) gx -= nm;
+    if (gy >= nm) gy -= nm;
+    const float* f = comp == 0 ? f0 : (comp == 1 ? f1 : f2);
+    const float* row = f + ((long long)gx * nm + gy) * rs;
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(fsm + r * hp);
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(sa),
+                 "l"(row + t.z0), "r"(zl * 4), "r"(bar_sa)
+                 : "memory");
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa + 4u * zl), "l"(row + gzz) : "memory");
+  }
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+// Bounded wait for phase `parity` of the mbarrier at bar_sa; false if the limit was reached.
+__device__ __forceinline__ bool bulk_wait(unsigned bar_sa, unsigned parity) {
+  for (int it = 0; it < kBulkWaitLimit; ++it) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar_sa), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
 // Interpolate the staged forces at the tile's particles e0..e1 (and kick and drift).  Returns
 // whether a non-finite state was written.
 template <bool KICK, int LT, int LZ, bool F32>
@@ -595,9 +649,18 @@ __global__ void __launch_bounds__(kThreads) k_gather_tiles(ParticleGeom pg, BinG
     const unsigned sa = (unsigned)__cvta_generic_to_shared(ent_s + i);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(ent_p + e0 + i) : "memory");
   }
-  gather_stage<LT, LZ>(fsm, b, pg.n, t, f0, f1, f2, rs);
+  // the forces by bulk copies on an mbarrier placed after the staged entries (8-byte aligned)
+  const unsigned bar_sa = (unsigned)__cvta_generic_to_shared(ent_s + kGatherEnt);
+  gather_stage_bulk<LT, LZ>(fsm, bar_sa, b, pg.n, t, f0, f1, f2, rs);
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-  __syncthreads();
+  const bool ok = bulk_wait(bar_sa, 0);
+  if (__syncthreads_or(!ok)) {
+    // the staging never completed (not expected): report, give the copies one more bounded wait, stop
+    if (threadIdx.x == 0) atomicOr(flags, 4);
+    bulk_wait(bar_sa, 0);
+    return;
+  }
+  if (threadIdx.x == 0) asm volatile("mbarrier.inval.shared::cta.b64 [%0];\n" ::"r"(bar_sa) : "memory");
   const bool bad = gather_particles<KICK, LT, LZ, F32>(fsm, pg, b, fg, t, e0, e1, ent_p, ent_s, ne, s_in, force_out,
                                                        s, v, psi1, psi2, kd);
   if (KICK && __syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flags, 2);
@@ -764,7 +827,7 @@ int launch_gather_tiles(const ParticleGeom& pg, const BinGeom& b, const BinBuffe
                         long long rs, const float* s_in, float* force_out, float* s, float* v, const float* psi1,
                         const float* psi2, const KickDrift* kd, int* flags, cudaStream_t st, bool pipelined) {
   const size_t sm = gather_smem_bytes(b);
-  const size_t sm_ent = (size_t)gather_floats(b) * sizeof(float) + kGatherEnt * sizeof(unsigned);
+  const size_t sm_ent = (size_t)gather_floats(b) * sizeof(float) + kGatherEnt * sizeof(unsigned) + 16;   // + mbarrier
   const KickDrift k = kd ? *kd : KickDrift{};
   const FixedGeo fg = fixed_geo(pg.n, pg.r_fixed);
   if (pipelined) {
